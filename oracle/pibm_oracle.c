@@ -1,0 +1,528 @@
+/*
+ * PIBM oracle: a plain, slow, double-precision CPU statement of one coupled
+ * LBM-PIBM-DEM time step of Zhang et al., "PIBM: Particulate immersed boundary
+ * method for fluid-particle interaction problems" (arXiv:1407.6704).
+ *
+ * TEST INFRASTRUCTURE. This file is the yardstick the CUDA library is checked
+ * against. Only the test suite, the smoke check and the benchmark's CPU
+ * baseline leg may load it. It shares no code, header, table generator or
+ * helper with the CUDA path, and the CUDA path never calls it.
+ *
+ * Equation numbers are the paper's printed numbers:
+ *   (1) velocity set, (2) BGK update, (3) equilibrium, (4) interpolation to a
+ *   particle, (5) Lagrange interpolant, (6) moving bounce-back, (7) force
+ *   density, (8) body-force term, (9) spreading, (10) discrete delta,
+ *   (11) one-dimensional kernel, (12) reaction force, (13) translation ODE.
+ *
+ * Frame and readings used throughout (the paper is silent on them):
+ *  - lattice units, h = 1, dt = 1, c = 1, c_s^2 = 1/3;
+ *  - node k on an axis sits at coordinate k + 1/2; a wall axis of extent N has
+ *    walls at 0 and N (halfway bounce-back); a periodic axis wraps;
+ *  - f holds the post-stream (pre-collision) populations of step n, i.e. the
+ *    f(r, t) of Eq. (2);
+ *  - one step: interpolate the populations to every particle (Eq. 4), compute
+ *    the DEM contact force on the old positions, update the particle velocity
+ *    (implicit in the drag by default), form the force density with the
+ *    moving bounce-back (Eqs. 6-7), move the particle, spread A_p g into F
+ *    (Eq. 9), collide every cell with the Guo term (Eqs. 2, 3, 8), stream;
+ *  - Eq. (7) is read as the momentum exchange sum_beta e_beta [f_beta(new) -
+ *    f_beta(old)] at the particle, which equals 2 (rho_l U - j_l);
+ *  - the interpolation weights are the same per-axis kernel as the spreading
+ *    (2-point hat or the 4-point cosine of Eq. 11); taps that fall outside a
+ *    wall axis are dropped and the remaining weights are renormalised per axis;
+ *  - contacts: linear spring-dashpot normal force (k_n, restitution e), brute
+ *    force over all pairs, plus the walls; no tangential force, no rotation.
+ *
+ * Layouts: populations f[a * ncell + c], c = x + nx * (y + ny * z);
+ * force F[k * ncell + c]; particle vectors are AoS with d components.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAXQ 19
+#define OR_PI 3.14159265358979323846
+
+typedef struct {
+  int q;              /* 9 (D2Q9), 15 (D3Q15) or 19 (D3Q19) */
+  int n[3];           /* lattice extents; n[2] = 1 in 2D */
+  int periodic[3];    /* 1 = periodic axis, 0 = walls at 0 and n */
+  double tau;         /* relaxation time of Eq. (2) */
+  int delta_width;    /* 2 (hat) or 4 (cosine, Eq. 11) */
+  int implicit_drag;  /* 1: drag uses U^{n+1}; 0: drag uses U^n (explicit) */
+  double gravity[3];  /* acceleration acting on particles */
+  double kn;          /* contact spring stiffness */
+  double restitution; /* normal restitution coefficient */
+} or_params;
+
+typedef struct {
+  int d, q;
+  int e[OR_MAXQ][3];
+  double w[OR_MAXQ];
+  int opp[OR_MAXQ];
+} or_lattice_t;
+
+/* Velocity sets, Eq. (1). Opposite directions are adjacent: a = 2k-1, 2k. */
+static int or_lattice_get(int q, or_lattice_t* L) {
+  static const int e9[9][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
+                               {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}};
+  static const int e15[15][3] = {{0, 0, 0},   {1, 0, 0},   {-1, 0, 0},  {0, 1, 0},  {0, -1, 0},
+                                 {0, 0, 1},   {0, 0, -1},  {1, 1, 1},   {-1, -1, -1}, {1, 1, -1},
+                                 {-1, -1, 1}, {1, -1, 1},  {-1, 1, -1}, {-1, 1, 1}, {1, -1, -1}};
+  static const int e19[19][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},   {0, -1, 0},
+                                 {0, 0, 1},  {0, 0, -1}, {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                                 {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                                 {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+  const int(*e)[3];
+  if (q == 9) {
+    e = e9;
+    L->d = 2;
+  } else if (q == 15) {
+    e = e15;
+    L->d = 3;
+  } else if (q == 19) {
+    e = e19;
+    L->d = 3;
+  } else {
+    return -1;
+  }
+  L->q = q;
+  for (int a = 0; a < q; ++a) {
+    int s = 0;
+    for (int k = 0; k < 3; ++k) {
+      L->e[a][k] = e[a][k];
+      s += e[a][k] * e[a][k];
+    }
+    /* weights by speed class */
+    if (q == 9) L->w[a] = (s == 0) ? 4.0 / 9.0 : (s == 1) ? 1.0 / 9.0 : 1.0 / 36.0;
+    if (q == 15) L->w[a] = (s == 0) ? 2.0 / 9.0 : (s == 1) ? 1.0 / 9.0 : 1.0 / 72.0;
+    if (q == 19) L->w[a] = (s == 0) ? 1.0 / 3.0 : (s == 1) ? 1.0 / 18.0 : 1.0 / 36.0;
+  }
+  for (int a = 0; a < q; ++a) {
+    L->opp[a] = -1;
+    for (int b = 0; b < q; ++b)
+      if (e[b][0] == -e[a][0] && e[b][1] == -e[a][1] && e[b][2] == -e[a][2]) L->opp[a] = b;
+  }
+  return 0;
+}
+
+int or_lattice(int q, int* d, int* e, double* w, int* opp) {
+  or_lattice_t L;
+  if (or_lattice_get(q, &L)) return -1;
+  *d = L.d;
+  for (int a = 0; a < q; ++a) {
+    for (int k = 0; k < 3; ++k) e[3 * a + k] = L.e[a][k];
+    w[a] = L.w[a];
+    opp[a] = L.opp[a];
+  }
+  return 0;
+}
+
+static long or_ncell(const or_params* p) { return (long)p->n[0] * p->n[1] * p->n[2]; }
+
+static long or_cell(const or_params* p, const int* x) {
+  return x[0] + (long)p->n[0] * (x[1] + (long)p->n[1] * x[2]);
+}
+
+/* One-dimensional kernels. 2-point: the linear hat (the 2-point Lagrange
+ * interpolant). 4-point: Eq. (11), 1/4 (1 + cos(pi a / 2)) for |a| <= 2. */
+double or_phi(int width, double a) {
+  double r = fabs(a);
+  if (width == 2) return r < 1.0 ? 1.0 - r : 0.0;
+  if (r > 2.0) return 0.0;
+  return 0.25 * (1.0 + cos(OR_PI * a / 2.0));
+}
+
+/* Taps and weights along one axis for a particle at coordinate X.
+ * b = floor(X - 1/2) is the node just below X; the 2-point stencil is {b, b+1},
+ * the 4-point one {b-1, ..., b+2}. Weight of node k: phi(k + 1/2 - X).
+ * Wall axis: taps outside [0, N-1] are dropped and the kept weights are
+ * divided by their sum. Periodic axis: indices wrap. Returns the tap count. */
+int or_taps(const or_params* p, int axis, double X, int* idx, double* w) {
+  int N = p->n[axis];
+  int b = (int)floor(X - 0.5);
+  int first = (p->delta_width == 2) ? b : b - 1;
+  int cnt = 0;
+  double sum = 0.0;
+  for (int t = 0; t < p->delta_width; ++t) {
+    int k = first + t;
+    double wk = or_phi(p->delta_width, (double)k + 0.5 - X);
+    if (p->periodic[axis]) {
+      int kk = ((k % N) + N) % N;
+      idx[cnt] = kk;
+      w[cnt] = wk;
+      ++cnt;
+    } else if (k >= 0 && k < N) {
+      idx[cnt] = k;
+      w[cnt] = wk;
+      sum += wk;
+      ++cnt;
+    }
+  }
+  if (!p->periodic[axis]) {
+    for (int t = 0; t < cnt; ++t) w[t] /= sum;
+  }
+  return cnt;
+}
+
+/* Macroscopic moments of the stored populations: rho = sum f, j = sum e f. */
+void or_moments(const or_params* p, const double* f, double* rho, double* j) {
+  or_lattice_t L;
+  or_lattice_get(p->q, &L);
+  long nc = or_ncell(p);
+  for (long c = 0; c < nc; ++c) {
+    double r = 0.0, m[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < L.q; ++a) {
+      double v = f[a * nc + c];
+      r += v;
+      for (int k = 0; k < L.d; ++k) m[k] += L.e[a][k] * v;
+    }
+    rho[c] = r;
+    for (int k = 0; k < L.d; ++k) j[k * nc + c] = m[k];
+  }
+}
+
+/* Eq. (4): every population interpolated to the particle position X with the
+ * tensor-product weights of the per-axis taps. */
+void or_interp_pops(const or_params* p, const double* f, const double* X, double* fl) {
+  or_lattice_t L;
+  or_lattice_get(p->q, &L);
+  long nc = or_ncell(p);
+  int idx[3][4], cnt[3] = {1, 1, 1};
+  double w[3][4];
+  idx[2][0] = 0;
+  w[2][0] = 1.0;
+  for (int k = 0; k < L.d; ++k) cnt[k] = or_taps(p, k, X[k], idx[k], w[k]);
+  for (int a = 0; a < L.q; ++a) fl[a] = 0.0;
+  for (int tz = 0; tz < cnt[2]; ++tz)
+    for (int ty = 0; ty < cnt[1]; ++ty)
+      for (int tx = 0; tx < cnt[0]; ++tx) {
+        int x[3] = {idx[0][tx], idx[1][ty], idx[2][tz]};
+        double wt = w[0][tx] * w[1][ty] * w[2][tz];
+        long c = or_cell(p, x);
+        for (int a = 0; a < L.q; ++a) fl[a] += wt * f[a * nc + c];
+      }
+}
+
+static double or_mass(int d, double dia, double rr) {
+  if (d == 2) return rr * OR_PI * dia * dia / 4.0; /* per unit depth */
+  return rr * OR_PI * dia * dia * dia / 6.0;
+}
+
+/* Minimum-image separation on periodic axes. */
+static double or_sep(const or_params* p, int k, double a, double b) {
+  double s = a - b;
+  if (p->periodic[k]) {
+    double N = (double)p->n[k];
+    if (s > 0.5 * N) s -= N;
+    if (s < -0.5 * N) s += N;
+  }
+  return s;
+}
+
+/* Contact force on particle i: linear spring-dashpot along the normal, summed
+ * over every other particle (brute force, ascending index) and over the walls.
+ * gamma = 2 beta sqrt(m_eff kn), beta = -ln e / sqrt(pi^2 + ln^2 e). */
+void or_contact_force(const or_params* p, long np, const double* X, const double* U,
+                      const double* dia, const double* rr, long i, double* Fc) {
+  int d = (p->q == 9) ? 2 : 3;
+  double lne = log(p->restitution);
+  double beta = -lne / sqrt(OR_PI * OR_PI + lne * lne);
+  double mi = or_mass(d, dia[i], rr[i]);
+  double ri = 0.5 * dia[i];
+  for (int k = 0; k < d; ++k) Fc[k] = 0.0;
+  for (long jx = 0; jx < np; ++jx) {
+    if (jx == i) continue;
+    double s[3], dist2 = 0.0;
+    for (int k = 0; k < d; ++k) {
+      s[k] = or_sep(p, k, X[i * d + k], X[jx * d + k]);
+      dist2 += s[k] * s[k];
+    }
+    double dist = sqrt(dist2);
+    double delta = ri + 0.5 * dia[jx] - dist;
+    if (delta <= 0.0 || dist <= 0.0) continue;
+    double mj = or_mass(d, dia[jx], rr[jx]);
+    double meff = mi * mj / (mi + mj);
+    double gam = 2.0 * beta * sqrt(meff * p->kn);
+    double vn = 0.0;
+    for (int k = 0; k < d; ++k) vn += (U[i * d + k] - U[jx * d + k]) * (s[k] / dist);
+    double mag = p->kn * delta - gam * vn;
+    for (int k = 0; k < d; ++k) Fc[k] += mag * (s[k] / dist);
+  }
+  double gw = 2.0 * beta * sqrt(mi * p->kn);
+  for (int k = 0; k < d; ++k) {
+    if (p->periodic[k]) continue;
+    /* wall at 0, normal +e_k */
+    double delta = ri - X[i * d + k];
+    if (delta > 0.0) Fc[k] += p->kn * delta - gw * U[i * d + k];
+    /* wall at N, normal -e_k */
+    delta = ri - ((double)p->n[k] - X[i * d + k]);
+    if (delta > 0.0) Fc[k] -= p->kn * delta - gw * (-U[i * d + k]);
+  }
+}
+
+/* Particle phase for particle i (§2.2-2.3), from the step-n state:
+ * outputs X^{n+1}, U^{n+1}, the force density g (Eq. 7) and the contact force.
+ * diag[0] receives |g_literal - 2 (rho_l U - j_l)| (max over components).
+ * Returns 1 if the particle left the domain through a wall, else 0. */
+int or_particle_update(const or_params* p, const double* f, long np, const double* X,
+                       const double* U, const double* dia, const double* rr, long i,
+                       double* Xn, double* Un, double* g, double* Fc, double* diag) {
+  or_lattice_t L;
+  or_lattice_get(p->q, &L);
+  int d = L.d;
+  double fl[OR_MAXQ];
+  or_interp_pops(p, f, X + i * d, fl); /* Eq. (4) */
+  double rho_l = 0.0, j_l[3] = {0.0, 0.0, 0.0};
+  for (int a = 0; a < L.q; ++a) {
+    rho_l += fl[a];
+    for (int k = 0; k < d; ++k) j_l[k] += L.e[a][k] * fl[a];
+  }
+  or_contact_force(p, np, X, U, dia, rr, i, Fc);
+  double m = or_mass(d, dia[i], rr[i]);
+  double Ap = OR_PI * dia[i] * dia[i] / 4.0;
+  double buoy = m * (1.0 - 1.0 / rr[i]); /* Eq. (13): (1 - rho_f / rho_p) m g */
+  double Ub[3];                           /* velocity seen by the bounce-back */
+  for (int k = 0; k < d; ++k) {
+    double Uo = U[i * d + k];
+    if (p->implicit_drag) {
+      /* m (U' - U) = buoy g + Fc - A_p * 2 (rho_l U' - j_l), solved for U' */
+      Un[k] = (m * Uo + 2.0 * Ap * j_l[k] + buoy * p->gravity[k] + Fc[k]) /
+              (m + 2.0 * Ap * rho_l);
+      Ub[k] = Un[k];
+    } else {
+      Un[k] = Uo + (buoy * p->gravity[k] + Fc[k] - Ap * 2.0 * (rho_l * Uo - j_l[k])) / m;
+      Ub[k] = Uo;
+    }
+  }
+  /* Eq. (6): population bounced into beta = opposite(alpha) by the moving
+   * particle; Eq. (7): momentum exchanged, sum_beta e_beta (new - old). */
+  double fnew[OR_MAXQ];
+  for (int a = 0; a < L.q; ++a) {
+    double eu = 0.0;
+    for (int k = 0; k < d; ++k) eu += L.e[a][k] * Ub[k];
+    fnew[L.opp[a]] = fl[a] - 2.0 * L.w[a] * rho_l * eu * 3.0; /* 1 / c_s^2 = 3 */
+  }
+  double dev = 0.0;
+  for (int k = 0; k < d; ++k) {
+    double s = 0.0;
+    for (int b = 0; b < L.q; ++b) s += L.e[b][k] * (fnew[b] - fl[b]);
+    g[k] = s;
+    double closed = 2.0 * (rho_l * Ub[k] - j_l[k]);
+    double dd = fabs(s - closed);
+    if (dd > dev) dev = dd;
+  }
+  if (diag) diag[0] = dev;
+  int escaped = 0;
+  for (int k = 0; k < d; ++k) {
+    double x = X[i * d + k] + Un[k];
+    if (p->periodic[k]) {
+      double N = (double)p->n[k];
+      if (x < 0.0) x += N;
+      else if (x >= N) x -= N;
+    } else if (x < 0.0 || x > (double)p->n[k]) {
+      escaped = 1;
+    }
+    Xn[k] = x;
+  }
+  return escaped;
+}
+
+/* Eq. (9): add A_p g D(r - X) to the force field F for one particle, with the
+ * same per-axis taps and weights as the interpolation (h = 1). */
+void or_spread_one(const or_params* p, const double* X, double dia, const double* g, double* F) {
+  int d = (p->q == 9) ? 2 : 3;
+  long nc = or_ncell(p);
+  double Ap = OR_PI * dia * dia / 4.0;
+  int idx[3][4], cnt[3] = {1, 1, 1};
+  double w[3][4];
+  idx[2][0] = 0;
+  w[2][0] = 1.0;
+  for (int k = 0; k < d; ++k) cnt[k] = or_taps(p, k, X[k], idx[k], w[k]);
+  for (int tz = 0; tz < cnt[2]; ++tz)
+    for (int ty = 0; ty < cnt[1]; ++ty)
+      for (int tx = 0; tx < cnt[0]; ++tx) {
+        int x[3] = {idx[0][tx], idx[1][ty], idx[2][tz]};
+        double wt = w[0][tx] * w[1][ty] * w[2][tz];
+        long c = or_cell(p, x);
+        for (int k = 0; k < d; ++k) F[k * nc + c] += Ap * g[k] * wt;
+      }
+}
+
+/* Collision of one cell, Eqs. (2), (3), (8): u = (j + F/2) / rho, equilibrium,
+ * Guo body-force term, relaxation. fc: the q populations of the cell (in),
+ * Fc: the d force components, out: post-collision populations. */
+static void or_collide_cell(const or_lattice_t* L, double tau, const double* fc, const double* Fc,
+                            double* out) {
+  int d = L->d;
+  double rho = 0.0, j[3] = {0.0, 0.0, 0.0}, u[3] = {0.0, 0.0, 0.0};
+  for (int a = 0; a < L->q; ++a) {
+    rho += fc[a];
+    for (int k = 0; k < d; ++k) j[k] += L->e[a][k] * fc[a];
+  }
+  double uu = 0.0;
+  for (int k = 0; k < d; ++k) {
+    u[k] = (j[k] + 0.5 * Fc[k]) / rho;
+    uu += u[k] * u[k];
+  }
+  for (int a = 0; a < L->q; ++a) {
+    double eu = 0.0, eF = 0.0, emuF = 0.0;
+    for (int k = 0; k < d; ++k) {
+      eu += L->e[a][k] * u[k];
+      eF += L->e[a][k] * Fc[k];
+      emuF += (L->e[a][k] - u[k]) * Fc[k];
+    }
+    double feq = rho * L->w[a] * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+    double Fb = (1.0 - 1.0 / (2.0 * tau)) * L->w[a] * (3.0 * emuF + 9.0 * eu * eF);
+    out[a] = fc[a] - (fc[a] - feq) / tau + Fb;
+  }
+}
+
+void or_collide(const or_params* p, const double* f, const double* F, double* fs) {
+  or_lattice_t L;
+  or_lattice_get(p->q, &L);
+  long nc = or_ncell(p);
+  double fc[OR_MAXQ], out[OR_MAXQ], Fc[3];
+  for (long c = 0; c < nc; ++c) {
+    for (int a = 0; a < L.q; ++a) fc[a] = f[a * nc + c];
+    for (int k = 0; k < L.d; ++k) Fc[k] = F ? F[k * nc + c] : 0.0;
+    or_collide_cell(&L, p->tau, fc, Fc, out);
+    for (int a = 0; a < L.q; ++a) fs[a * nc + c] = out[a];
+  }
+}
+
+/* Source of population a arriving at cell x: x - e_a, wrapped on periodic
+ * axes. Returns 0 and the source cell, or 1 when the link crosses a wall
+ * (halfway bounce-back: the arriving value is fs[opp(a)] at x itself). */
+static int or_source(const or_params* p, const or_lattice_t* L, const int* x, int a, int* src) {
+  for (int k = 0; k < 3; ++k) {
+    int s = x[k] - L->e[a][k];
+    if (p->periodic[k]) {
+      s = ((s % p->n[k]) + p->n[k]) % p->n[k];
+    } else if (s < 0 || s >= p->n[k]) {
+      return 1;
+    }
+    src[k] = s;
+  }
+  return 0;
+}
+
+/* Streaming, the left-hand side of Eq. (2), as a pull with halfway
+ * bounce-back at resting walls. */
+void or_stream(const or_params* p, const double* fs, double* f) {
+  or_lattice_t L;
+  or_lattice_get(p->q, &L);
+  long nc = or_ncell(p);
+  int x[3], src[3];
+  for (x[2] = 0; x[2] < p->n[2]; ++x[2])
+    for (x[1] = 0; x[1] < p->n[1]; ++x[1])
+      for (x[0] = 0; x[0] < p->n[0]; ++x[0]) {
+        long c = or_cell(p, x);
+        for (int a = 0; a < L.q; ++a) {
+          if (or_source(p, &L, x, a, src))
+            f[a * nc + c] = fs[L.opp[a] * nc + c];
+          else
+            f[a * nc + c] = fs[a * nc + or_cell(p, src)];
+        }
+      }
+}
+
+/* One full step in the order stated at the top of this file. f is advanced
+ * in place (fs is scratch of the same size); X, U are replaced by the new
+ * state. F receives the spread force of this step; g, Fc the per-particle
+ * force density and contact force. diag[0]: max literal-vs-closed g deviation;
+ * diag[1]: number of escaped particles. */
+void or_step(const or_params* p, double* f, double* fs, double* F, long np, double* X, double* U,
+             const double* dia, const double* rr, double* Xn, double* Un, double* g, double* Fc,
+             double* diag) {
+  int d = (p->q == 9) ? 2 : 3;
+  long nc = or_ncell(p);
+  double dev_max = 0.0, esc = 0.0;
+  for (long i = 0; i < np; ++i) {
+    double dv = 0.0;
+    esc += or_particle_update(p, f, np, X, U, dia, rr, i, Xn + i * d, Un + i * d, g + i * d,
+                              Fc + i * d, &dv);
+    if (dv > dev_max) dev_max = dv;
+  }
+  memset(F, 0, sizeof(double) * d * nc);
+  for (long i = 0; i < np; ++i) or_spread_one(p, X + i * d, dia[i], g + i * d, F);
+  or_collide(p, f, F, fs);
+  or_stream(p, fs, f);
+  memcpy(X, Xn, sizeof(double) * np * d);
+  memcpy(U, Un, sizeof(double) * np * d);
+  if (diag) {
+    if (dev_max > diag[0]) diag[0] = dev_max;
+    diag[1] += esc;
+  }
+}
+
+void or_run(const or_params* p, long nsteps, double* f, double* fs, double* F, long np, double* X,
+            double* U, const double* dia, const double* rr, double* Xn, double* Un, double* g,
+            double* Fc, double* diag) {
+  for (long s = 0; s < nsteps; ++s) or_step(p, f, fs, F, np, X, U, dia, rr, Xn, Un, g, Fc, diag);
+}
+
+/* Sampled evaluation for large lattices. */
+
+/* F at one cell after the particle phase: the sum over every particle whose
+ * stencil covers the cell, in ascending particle index, of A_p g w. */
+void or_force_at_cell(const or_params* p, const double* f, long np, const double* X,
+                      const double* U, const double* dia, const double* rr, long cell,
+                      double* Fout) {
+  int d = (p->q == 9) ? 2 : 3;
+  int x[3] = {(int)(cell % p->n[0]), (int)((cell / p->n[0]) % p->n[1]),
+              (int)(cell / ((long)p->n[0] * p->n[1]))};
+  for (int k = 0; k < d; ++k) Fout[k] = 0.0;
+  for (long i = 0; i < np; ++i) {
+    int idx[3][4], cnt[3] = {1, 1, 1};
+    double w[3][4];
+    idx[2][0] = 0;
+    w[2][0] = 1.0;
+    for (int k = 0; k < d; ++k) cnt[k] = or_taps(p, k, X[i * d + k], idx[k], w[k]);
+    double wt = 0.0;
+    int hit = 0;
+    for (int tz = 0; tz < cnt[2]; ++tz)
+      for (int ty = 0; ty < cnt[1]; ++ty)
+        for (int tx = 0; tx < cnt[0]; ++tx)
+          if (idx[0][tx] == x[0] && idx[1][ty] == x[1] && idx[2][tz] == x[2]) {
+            wt += w[0][tx] * w[1][ty] * w[2][tz];
+            hit = 1;
+          }
+    if (!hit) continue;
+    double Xn[3], Un[3], gg[3], Fc[3];
+    or_particle_update(p, f, np, X, U, dia, rr, i, Xn, Un, gg, Fc, NULL);
+    double Ap = OR_PI * dia[i] * dia[i] / 4.0;
+    for (int k = 0; k < d; ++k) Fout[k] += Ap * gg[k] * wt;
+  }
+}
+
+/* Post-step populations at one cell: each arriving population is the
+ * post-collision value at its source (or the bounced one at the cell itself);
+ * the collision at a source needs F there, evaluated with or_force_at_cell. */
+void or_cell_after_step(const or_params* p, const double* f, long np, const double* X,
+                        const double* U, const double* dia, const double* rr, long cell,
+                        double* out) {
+  or_lattice_t L;
+  or_lattice_get(p->q, &L);
+  long nc = or_ncell(p);
+  int x[3] = {(int)(cell % p->n[0]), (int)((cell / p->n[0]) % p->n[1]),
+              (int)(cell / ((long)p->n[0] * p->n[1]))};
+  int src[3];
+  double fc[OR_MAXQ], post[OR_MAXQ], Fc[3];
+  for (int a = 0; a < L.q; ++a) {
+    long sc;
+    int b;
+    if (or_source(p, &L, x, a, src)) {
+      sc = cell;
+      b = L.opp[a];
+    } else {
+      sc = or_cell(p, src);
+      b = a;
+    }
+    for (int k = 0; k < L.q; ++k) fc[k] = f[k * nc + sc];
+    or_force_at_cell(p, f, np, X, U, dia, rr, sc, Fc);
+    or_collide_cell(&L, p->tau, fc, Fc, post);
+    out[a] = post[b];
+  }
+}

@@ -1,0 +1,206 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the smoke check.
+
+This module holds no arithmetic of the method: it draws particle positions,
+diameters and density ratios (uniform random, non-overlapping, inside a band of
+the domain) and random population fields around a base vector that the caller
+supplies. Both the CUDA path and the oracle receive exactly these arrays.
+
+Workload presets mirror the sedimentation set-ups used for measurement:
+  c1  2D D2Q9 128x128, walls, tau 0.8, 200 particles d=0.5, rho_p/rho_f=2, top half,
+      gravity 1e-5, 2-point delta
+  c2  2D D2Q9 2048x2048, walls, tau 0.6, 500k particles d~U[0.3,0.8], ratio 2.5,
+      top 60 %, 4-point delta
+  c3  3D D3Q19 256^3, walls, tau 0.55, 4M particles d=0.6, ratio 2, top half, 4-point
+  c3s the 64^3 slice of c3 with the same particle density (62,500 particles)
+  c5  3D D3Q19 96^3, walls, tau 0.7, 20k particles d=0.5, ratio 2, top half, 4-point
+Contacts: linear spring-dashpot, kn = 1e-2, restitution 0.9, everywhere.
+"""
+from dataclasses import dataclass, field
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+
+@dataclass
+class Workload:
+    name: str
+    q: int
+    n: Tuple[int, ...]
+    periodic: Tuple[int, ...]
+    tau: float
+    delta_width: int
+    gravity: Tuple[float, ...]
+    n_particles: int
+    diameter: object          # float or (lo, hi)
+    density_ratio: object     # float or (lo, hi)
+    band: Tuple[float, float]  # fraction of the gravity axis holding particles
+    seed: int
+    kn: float = 1e-2
+    restitution: float = 0.9
+    steps: int = 1000
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def d(self):
+        return len(self.n)
+
+    @property
+    def ncell(self):
+        return int(np.prod(self.n))
+
+
+def preset(name: str) -> Workload:
+    g2 = (0.0, -1e-5)
+    g3 = (0.0, 0.0, -1e-5)
+    if name == "c1":
+        return Workload("c1", 9, (128, 128), (0, 0), 0.8, 2, g2, 200, 0.5, 2.0, (0.5, 1.0), 1,
+                        steps=1000)
+    if name == "c2":
+        return Workload("c2", 9, (2048, 2048), (0, 0), 0.6, 4, g2, 500_000, (0.3, 0.8), 2.5,
+                        (0.4, 1.0), 2, steps=10_000)
+    if name == "c3":
+        return Workload("c3", 19, (256, 256, 256), (0, 0, 0), 0.55, 4, g3, 4_000_000, 0.6, 2.0,
+                        (0.5, 1.0), 3)
+    if name == "c3s":
+        return Workload("c3s", 19, (64, 64, 64), (0, 0, 0), 0.55, 4, g3, 62_500, 0.6, 2.0,
+                        (0.5, 1.0), 3)
+    if name == "c5":
+        return Workload("c5", 19, (96, 96, 96), (0, 0, 0), 0.7, 4, g3, 20_000, 0.5, 2.0,
+                        (0.5, 1.0), 5, steps=500)
+    raise KeyError(name)
+
+
+def _draw(rng, spec, n):
+    if np.isscalar(spec):
+        return np.full(n, float(spec))
+    lo, hi = spec
+    return rng.uniform(lo, hi, n)
+
+
+def sample_particles(n: Sequence[int], n_particles: int, diameter, density_ratio,
+                     band=(0.5, 1.0), seed=0, slots=None, max_rounds=400):
+    """Uniform random, pairwise non-overlapping particles.
+
+    Positions are drawn uniformly in a box that keeps every particle at least
+    half the largest diameter away from each face of the domain; along the last
+    axis (the gravity axis) the box is further restricted to ``band`` (fractions
+    of the extent). A candidate is kept when it overlaps no kept particle; within
+    one round of candidates the lower index wins. Returns X (np, d), diameter (np,),
+    density ratio (np,), all float64.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    d = len(n)
+    dia = _draw(rng, diameter, n_particles)
+    rr = _draw(rng, density_ratio, n_particles)
+    if n_particles == 0:
+        return np.zeros((0, d)), dia, rr
+    dmax = float(dia.max())
+    cs = max(1.0, float(np.ceil(dmax)))  # grid cell size >= largest contact distance
+    lo = np.full(d, 0.5 * dmax)
+    hi = np.array(n, dtype=np.float64) - 0.5 * dmax
+    lo[-1] = max(lo[-1], band[0] * n[-1])
+    hi[-1] = min(hi[-1], band[1] * n[-1])
+    if np.any(hi <= lo):
+        raise ValueError("empty placement region")
+    gdim = np.ceil(np.array(n, dtype=np.float64) / cs).astype(np.int64)
+    ngc = int(np.prod(gdim))
+    K = slots or (6 if d == 2 else 4)
+    grid = np.full((ngc, K), -1, dtype=np.int32)
+    fill = np.zeros(ngc, dtype=np.int64)
+    X = np.zeros((n_particles, d))
+    placed = np.zeros(n_particles, dtype=bool)
+    offs = np.array(np.meshgrid(*([[-1, 0, 1]] * d), indexing="ij")).reshape(d, -1).T
+
+    def gcoord(P):
+        return np.minimum((P / cs).astype(np.int64), gdim - 1)
+
+    def flat(gc):
+        idx = gc[:, -1]
+        for k in range(d - 2, -1, -1):
+            idx = idx * gdim[k] + gc[:, k]
+        return idx
+
+    for _ in range(max_rounds):
+        todo = np.nonzero(~placed)[0]
+        if todo.size == 0:
+            break
+        cand = lo + (hi - lo) * rng.random((todo.size, d))
+        gc = gcoord(cand)
+        ok = np.ones(todo.size, dtype=bool)
+        # against particles already kept
+        for o in offs:
+            nb = gc + o
+            inside = np.all((nb >= 0) & (nb < gdim), axis=1)
+            nbf = flat(np.where(inside[:, None], nb, 0))
+            for s in range(K):
+                other = grid[nbf, s]
+                valid = inside & (other >= 0)
+                if not valid.any():
+                    continue
+                oi = np.where(valid, other, 0)
+                dist = np.linalg.norm(cand - X[oi], axis=1)
+                clash = valid & (dist < 0.5 * (dia[todo] + dia[oi]))
+                ok &= ~clash
+        # within this round: lower index wins
+        sel = np.nonzero(ok)[0]
+        if sel.size:
+            cf = flat(gc[sel])
+            order = np.lexsort((sel, cf))
+            sc = cf[order]
+            ss = sel[order]
+            start = np.searchsorted(sc, sc, side="left")
+            rank = np.arange(sc.size) - start
+            Kt = int(rank.max()) + 1
+            tmp = np.full((ngc, Kt), -1, dtype=np.int32)
+            tmp[sc, rank] = ss
+            for o in offs:
+                nb = gc[sel] + o
+                inside = np.all((nb >= 0) & (nb < gdim), axis=1)
+                nbf = flat(np.where(inside[:, None], nb, 0))
+                for s in range(Kt):
+                    other = tmp[nbf, s]
+                    valid = inside & (other >= 0) & (other < sel)
+                    if not valid.any():
+                        continue
+                    oi = np.where(valid, other, 0)
+                    dist = np.linalg.norm(cand[sel] - cand[oi], axis=1)
+                    clash = valid & (dist < 0.5 * (dia[todo[sel]] + dia[todo[oi]]))
+                    ok[sel[clash]] = False
+        # insert the survivors, respecting the per-cell slot limit
+        sel = np.nonzero(ok)[0]
+        if sel.size:
+            cf = flat(gc[sel])
+            order = np.lexsort((sel, cf))
+            sc = cf[order]
+            ss = sel[order]
+            start = np.searchsorted(sc, sc, side="left")
+            slot = fill[sc] + (np.arange(sc.size) - start)
+            keep = slot < K
+            sc, ss, slot = sc[keep], ss[keep], slot[keep]
+            pid = todo[ss]
+            grid[sc, slot] = pid
+            X[pid] = cand[ss]
+            placed[pid] = True
+            np.add.at(fill, sc, 1)
+            fill = np.minimum(fill, K)
+    if not placed.all():
+        raise RuntimeError(f"could not place {np.count_nonzero(~placed)} particles")
+    return X, dia, rr
+
+
+def workload_particles(w: Workload, n_particles: Optional[int] = None):
+    npart = w.n_particles if n_particles is None else n_particles
+    return sample_particles(w.n, npart, w.diameter, w.density_ratio, w.band, w.seed)
+
+
+def populations(base, shape, seed=0, eps=1e-2):
+    """Random positive populations base[a] * (1 + eps * r), r ~ U(-1, 1)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    base = np.asarray(base, dtype=np.float64)
+    r = rng.uniform(-1.0, 1.0, (base.size,) + tuple(shape))
+    return base.reshape((-1,) + (1,) * len(shape)) * (1.0 + eps * r)
+
+
+def velocities(n_particles, d, seed=0, scale=1e-3):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return scale * rng.uniform(-1.0, 1.0, (n_particles, d))
