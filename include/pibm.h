@@ -1,0 +1,174 @@
+/*
+ * pibm.h — C ABI of the GB300 library for the coupled LBM-PIBM-DEM time step of
+ * Zhang et al., "PIBM: Particulate immersed boundary method for fluid-particle
+ * interaction problems" (arXiv:1407.6704).
+ *
+ * One step of the method (section 2 of the paper):
+ *   1. the fluid moments at every particle are interpolated from the lattice
+ *      (Eq. 4; the interpolant is the same per-axis kernel as the spreading);
+ *   2. the particle velocity is advanced under buoyancy-reduced gravity, the
+ *      contact force and the fluid force (Eq. 13); the fluid force is the
+ *      reaction -A_p g (Eq. 12) of the force density g that a moving bounce-back
+ *      with the particle velocity exchanges with the fluid (Eqs. 6-7), which is
+ *      g = 2 (rho_l U - j_l);
+ *   3. A_p g is spread back to the lattice with the discrete delta (Eqs. 9-11);
+ *   4. every cell collides with the BGK rule and the Guo body-force term
+ *      (Eqs. 2, 3, 8; velocity u = (j + F/2) / rho) and streams.
+ * Contacts are the linear spring-dashpot normal force (stiffness kn,
+ * restitution e) between overlapping particles and against walls, found over a
+ * cell list of lattice-sized bins. Units are lattice units (h = 1, dt = 1).
+ *
+ * Conventions shared by every call:
+ *  - Status codes: PIBM_OK (0) on success, a negative PIBM_E* value otherwise;
+ *    pibm_strerror() names it. A failed call leaves the handle usable unless it
+ *    returns PIBM_ECUDA (the CUDA context may be lost).
+ *  - Lattice node k of an axis sits at coordinate k + 1/2; a wall axis of extent
+ *    N has resting walls at 0 and N (halfway bounce-back); a periodic axis wraps.
+ *  - Cell index c = x + n[0] * (y + n[1] * z).
+ *  - Velocity sets, in this order (opposites adjacent):
+ *      D2Q9 : (0,0) (1,0) (-1,0) (0,1) (0,-1) (1,1) (-1,-1) (1,-1) (-1,1)
+ *      D3Q15: 0, +-x, +-y, +-z, (1,1,1) (-1,-1,-1) (1,1,-1) (-1,-1,1) (1,-1,1)
+ *             (-1,1,-1) (-1,1,1) (1,-1,-1)
+ *      D3Q19: 0, +-x, +-y, +-z, (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1)
+ *             (-1,0,-1) (1,0,-1) (-1,0,1) (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1)
+ *  - Field arrays are structure-of-arrays FP64: populations [q][ncell],
+ *    vectors [d][ncell]; particle arrays are AoS FP64 [n_particles][d].
+ *  - The caller keeps ownership of every array it passes; the library copies
+ *    what it needs during the call.
+ *  - A handle is bound to the CUDA device that was current at pibm_create and
+ *    to one stream; calls on one handle must not overlap (not thread-safe).
+ */
+#ifndef PIBM_H
+#define PIBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define PIBM_OK 0
+#define PIBM_EINVAL (-1)    /* bad argument or configuration */
+#define PIBM_ENOMEM (-2)    /* workspace too small or allocation failed */
+#define PIBM_ECUDA (-3)     /* a CUDA call failed */
+#define PIBM_EUNSTABLE (-4) /* non-finite fluid or particle state detected */
+#define PIBM_EESCAPED (-5)  /* a particle crossed a wall */
+#define PIBM_ENOTSUP (-6)   /* combination not built into this library */
+
+/* lattices (value = number of velocities q) */
+#define PIBM_D2Q9 9
+#define PIBM_D3Q15 15
+#define PIBM_D3Q19 19
+
+/* per-axis boundary */
+#define PIBM_WALL 0
+#define PIBM_PERIODIC 1
+
+/* particle drag coupling */
+#define PIBM_IMPLICIT 0 /* force density evaluated with U^{n+1} (solved in closed form) */
+#define PIBM_EXPLICIT 1 /* force density evaluated with U^n */
+
+/* storage / arithmetic of the populations; particles, contacts and the
+ * particle integration are FP64 in every mode */
+#define PIBM_FP64 0 /* populations, collision and spread force in FP64 */
+#define PIBM_FP32 1 /* populations stored as f - w in FP32, FP32 collision and force field */
+
+/* fields for pibm_read_fields (bit k selects dst[k]) */
+#define PIBM_FIELD_RHO (1u << 0) /* ncell: rho = sum_a f_a of the current state */
+#define PIBM_FIELD_J (1u << 1)   /* d*ncell: j = sum_a e_a f_a (no half-force term) */
+#define PIBM_FIELD_POP (1u << 2) /* q*ncell: post-stream populations f_a of the current state */
+#define PIBM_FIELD_X (1u << 3)   /* n_particles*d: particle positions */
+#define PIBM_FIELD_U (1u << 4)   /* n_particles*d: particle velocities */
+#define PIBM_NFIELDS 5
+/* The spread force field is consumed (and cleared) by the collision of the same
+ * step; its content is fixed by the per-particle force density, which
+ * pibm_forces returns as f_fpi = -A_p g. */
+
+typedef struct pibm_config {
+  int lattice;         /* PIBM_D2Q9, PIBM_D3Q15 or PIBM_D3Q19 */
+  int64_t n[3];        /* lattice extents; n[2] = 1 for D2Q9 */
+  int boundary[3];     /* PIBM_WALL or PIBM_PERIODIC per axis (ignored for z in 2D) */
+  double tau;          /* BGK relaxation time, Eq. (2); must exceed 1/2 */
+  double gravity[3];   /* acceleration on the particles; the fluid carries none */
+  int delta_width;     /* 2 (linear hat) or 4 (cosine kernel, Eq. 11) */
+  int coupling;        /* PIBM_IMPLICIT or PIBM_EXPLICIT */
+  int precision;       /* PIBM_FP64 or PIBM_FP32 */
+  int deterministic;   /* 0: spread with atomics; 1: ordered per-cell gather,
+                          bitwise reproducible run to run */
+  double dem_kn;       /* contact stiffness */
+  double dem_restitution; /* normal restitution coefficient, in (0, 1] */
+  int64_t n_particles; /* may be 0 */
+  const double* x0;    /* host, [n_particles][d]; every particle inside the
+                          domain and at least its radius from every wall */
+  const double* u0;    /* host, [n_particles][d], or NULL for particles at rest */
+  const double* diameter;      /* host, [n_particles], each in (0, 1] */
+  const double* density_ratio; /* host, [n_particles], rho_p / rho_f, > 0 */
+  const double* f0;    /* host, [q][ncell] post-stream populations of step 0, or
+                          NULL for the rest state f_a = w_a (rho = 1, u = 0) */
+} pibm_config;
+
+typedef struct pibm_t pibm_t; /* opaque handle owning the device state */
+
+/* Device bytes that pibm_create needs for this configuration.
+ * Returns PIBM_EINVAL for an invalid configuration. */
+int pibm_workspace_bytes(const pibm_config* cfg, size_t* bytes);
+
+/* Validate cfg, lay out the device state and upload the initial condition.
+ * workspace: device memory of at least pibm_workspace_bytes() bytes, 256-byte
+ *   aligned, owned by the caller and kept alive until pibm_destroy; or NULL, in
+ *   which case the library allocates (and later frees) it with cudaMalloc.
+ * stream: the cudaStream_t every later call is ordered on (NULL = legacy
+ *   default stream). Returns with the upload complete.
+ * Errors: PIBM_EINVAL (tau <= 1/2, bad lattice/width/precision, a particle
+ *   outside the domain or closer than its radius to a wall, diameter outside
+ *   (0, 1], NULL arrays with n_particles > 0), PIBM_ENOMEM, PIBM_ECUDA. */
+int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes, void* stream,
+                pibm_t** out);
+
+/* Advance nsteps coupled time steps, asynchronously on the handle's stream.
+ * Health flags raised on the device (non-finite state, escaped particle) are
+ * reported by the next synchronising call. */
+int pibm_step(pibm_t* h, int64_t nsteps);
+
+/* Per-particle forces of the last step, AoS [n_particles][d] FP64:
+ * f_fpi = -A_p g (Eq. 12), f_contact = the contact force. Either pointer may be
+ * NULL. on_device != 0: the pointers are device memory on the handle's device.
+ * Synchronises the stream; returns the device health status. */
+int pibm_forces(pibm_t* h, double* f_fpi, double* f_contact, int on_device);
+
+/* Copy the fields selected by mask into dst[k] (bit k of mask), FP64, layouts
+ * as documented at PIBM_FIELD_*. Entries of dst for unselected bits are ignored.
+ * Synchronises the stream; returns the device health status. */
+int pibm_read_fields(pibm_t* h, unsigned mask, void* const* dst, int on_device);
+
+/* Global invariants of the current state, FP64, reduced in a fixed order:
+ * out[0] = total mass sum rho, out[1..d] = fluid momentum sum j,
+ * out[1+d..2d] = particle momentum sum m U. Synchronises the stream. */
+int pibm_invariants(pibm_t* h, double* out);
+
+/* Synchronise the stream and return the device health status. */
+int pibm_status(pibm_t* h);
+
+/* Number of kernels one pibm_step(h, 1) launches (for launch accounting). */
+int pibm_kernels_per_step(pibm_t* h);
+
+/* Advance nsteps steps like pibm_step, launched one phase at a time with CUDA
+ * events between the phases, and return the summed device time of each phase
+ * in milliseconds: phase_ms[0] cell-list binning, phase_ms[1] particle phase
+ * (interpolation, contacts, update, spreading), phase_ms[2] fused
+ * stream-collide, phase_ms[3] the whole steps (first event to last).
+ * Synchronises the stream. Not part of the method; a timing aid. */
+int pibm_profile_steps(pibm_t* h, int64_t nsteps, double* phase_ms);
+
+/* Free the handle (and the workspace when the library allocated it). NULL is a no-op. */
+void pibm_destroy(pibm_t* h);
+
+const char* pibm_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIBM_H */

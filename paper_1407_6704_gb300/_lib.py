@@ -1,0 +1,108 @@
+"""ctypes declarations of the C ABI in ``include/pibm.h``.
+
+Argument marshalling only: every step of the method runs in ``libpibm.so``.
+Loading fails loudly when the library has not been built; there is no
+fallback implementation.
+"""
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_build", "libpibm.so")
+
+PIBM_OK = 0
+PIBM_EINVAL = -1
+PIBM_ENOMEM = -2
+PIBM_ECUDA = -3
+PIBM_EUNSTABLE = -4
+PIBM_EESCAPED = -5
+PIBM_ENOTSUP = -6
+
+PIBM_D2Q9, PIBM_D3Q15, PIBM_D3Q19 = 9, 15, 19
+PIBM_WALL, PIBM_PERIODIC = 0, 1
+PIBM_IMPLICIT, PIBM_EXPLICIT = 0, 1
+PIBM_FP64, PIBM_FP32 = 0, 1
+
+FIELD_RHO, FIELD_J, FIELD_POP, FIELD_X, FIELD_U = (1 << k for k in range(5))
+NFIELDS = 5
+
+# every symbol include/pibm.h declares
+EXPORTS = ["pibm_workspace_bytes", "pibm_create", "pibm_step", "pibm_forces",
+           "pibm_read_fields", "pibm_invariants", "pibm_status", "pibm_kernels_per_step",
+           "pibm_destroy", "pibm_strerror", "pibm_profile_steps"]
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class PibmConfig(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_int),
+        ("n", ctypes.c_int64 * 3),
+        ("boundary", ctypes.c_int * 3),
+        ("tau", ctypes.c_double),
+        ("gravity", ctypes.c_double * 3),
+        ("delta_width", ctypes.c_int),
+        ("coupling", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("deterministic", ctypes.c_int),
+        ("dem_kn", ctypes.c_double),
+        ("dem_restitution", ctypes.c_double),
+        ("n_particles", ctypes.c_int64),
+        ("x0", _dp),
+        ("u0", _dp),
+        ("diameter", _dp),
+        ("density_ratio", _dp),
+        ("f0", _dp),
+    ]
+
+
+class PibmError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        msg = load().pibm_strerror(status).decode()
+        super().__init__(f"{what}: {msg} (status {status})" if what else msg)
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libpibm.so once; raise if it is missing (build it with build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpibm.so not built at {path}; run paper_1407_6704_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    P = ctypes.POINTER(PibmConfig)
+    vp = ctypes.c_void_p
+    L.pibm_workspace_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+    L.pibm_workspace_bytes.restype = ctypes.c_int
+    L.pibm_create.argtypes = [P, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+    L.pibm_create.restype = ctypes.c_int
+    L.pibm_step.argtypes = [vp, ctypes.c_int64]
+    L.pibm_step.restype = ctypes.c_int
+    L.pibm_forces.argtypes = [vp, vp, vp, ctypes.c_int]
+    L.pibm_forces.restype = ctypes.c_int
+    L.pibm_read_fields.argtypes = [vp, ctypes.c_uint, ctypes.POINTER(vp), ctypes.c_int]
+    L.pibm_read_fields.restype = ctypes.c_int
+    L.pibm_invariants.argtypes = [vp, _dp]
+    L.pibm_invariants.restype = ctypes.c_int
+    L.pibm_status.argtypes = [vp]
+    L.pibm_status.restype = ctypes.c_int
+    L.pibm_kernels_per_step.argtypes = [vp]
+    L.pibm_kernels_per_step.restype = ctypes.c_int
+    L.pibm_profile_steps.argtypes = [vp, ctypes.c_int64, _dp]
+    L.pibm_profile_steps.restype = ctypes.c_int
+    L.pibm_destroy.argtypes = [vp]
+    L.pibm_destroy.restype = None
+    L.pibm_strerror.argtypes = [ctypes.c_int]
+    L.pibm_strerror.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def check(status, what=""):
+    if status != PIBM_OK:
+        raise PibmError(status, what)
+    return status

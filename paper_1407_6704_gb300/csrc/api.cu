@@ -1,0 +1,572 @@
+// Host side of the C ABI declared in include/pibm.h: validation, workspace
+// layout, upload of the initial state, the step loop (replayed from CUDA graphs
+// of two steps) and the read-back calls.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "pibm_internal.cuh"
+
+using namespace pibm;
+
+struct pibm_t {
+  State s;
+  cudaStream_t stream;     // caller's stream
+  cudaStream_t cap;        // private stream used for graph capture
+  void* ws;                // workspace base
+  size_t ws_bytes;
+  int owns_ws;
+  int device;
+  cudaGraphExec_t graph[2];  // two-step graphs, indexed by the parity of s.cur
+  int graph_failed;
+  double* out_dev;         // small device scratch for reductions
+  int kernels_per_step;
+};
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+
+size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+struct Layout {
+  size_t f, F, red, err, out, X, U, rad, mass, Ap, buoy, g, Fc, key, rank, perm, bin, bsum;
+  size_t total;
+};
+
+int dims_of(int lattice) { return lattice == PIBM_D2Q9 ? 2 : 3; }
+
+int validate(const pibm_config* c) {
+  if (!c) return PIBM_EINVAL;
+  if (c->lattice != PIBM_D2Q9 && c->lattice != PIBM_D3Q15 && c->lattice != PIBM_D3Q19)
+    return PIBM_EINVAL;
+  const int d = dims_of(c->lattice);
+  long long ncell = 1;
+  for (int k = 0; k < 3; ++k) {
+    if (c->n[k] < 1 || c->n[k] > (1 << 30)) return PIBM_EINVAL;
+    if (k < d && c->boundary[k] != PIBM_WALL && c->boundary[k] != PIBM_PERIODIC)
+      return PIBM_EINVAL;
+    ncell *= c->n[k];
+  }
+  if (d == 2 && c->n[2] != 1) return PIBM_EINVAL;
+  // bins are cells; the cell-list scan covers up to 8192 * 8192 entries
+  if (ncell + 1 > 8192LL * 8192LL) return PIBM_ENOTSUP;
+  if (!(c->tau > 0.5) || !isfinite(c->tau)) return PIBM_EINVAL;
+  if (c->delta_width != 2 && c->delta_width != 4) return PIBM_EINVAL;
+  if (c->coupling != PIBM_IMPLICIT && c->coupling != PIBM_EXPLICIT) return PIBM_EINVAL;
+  if (c->precision != PIBM_FP64 && c->precision != PIBM_FP32) return PIBM_EINVAL;
+  if (!(c->dem_kn >= 0.0) || !isfinite(c->dem_kn)) return PIBM_EINVAL;
+  if (!(c->dem_restitution > 0.0 && c->dem_restitution <= 1.0)) return PIBM_EINVAL;
+  for (int k = 0; k < 3; ++k)
+    if (!isfinite(c->gravity[k])) return PIBM_EINVAL;
+  if (c->n_particles < 0 || c->n_particles > 0x7fffffffLL) return PIBM_EINVAL;
+  if (c->n_particles > 0) {
+    if (!c->x0 || !c->diameter || !c->density_ratio) return PIBM_EINVAL;
+    for (int k = 0; k < d; ++k)  // contact and spreading stencils must not alias
+      if (c->boundary[k] == PIBM_PERIODIC && c->n[k] < 5) return PIBM_EINVAL;
+    for (long long p = 0; p < c->n_particles; ++p) {
+      double dia = c->diameter[p], rr = c->density_ratio[p];
+      if (!(dia > 0.0 && dia <= 1.0)) return PIBM_EINVAL;
+      if (!(rr > 0.0) || !isfinite(rr)) return PIBM_EINVAL;
+      for (int k = 0; k < d; ++k) {
+        double x = c->x0[p * d + k];
+        if (!isfinite(x)) return PIBM_EINVAL;
+        if (c->boundary[k] == PIBM_PERIODIC) {
+          if (x < 0.0 || x >= (double)c->n[k]) return PIBM_EINVAL;
+        } else if (!(x > 0.0 && x < (double)c->n[k])) {
+          return PIBM_EINVAL;
+        }
+        if (c->u0 && !isfinite(c->u0[p * d + k])) return PIBM_EINVAL;
+      }
+    }
+  }
+  return PIBM_OK;
+}
+
+Layout layout(const pibm_config* c) {
+  Layout L;
+  const int q = c->lattice, d = dims_of(q);
+  const long long ncell = c->n[0] * c->n[1] * c->n[2];
+  const long long pitch = (ncell + 63) / 64 * 64;
+  const size_t ts = c->precision == PIBM_FP64 ? 8 : 4;
+  const long long np = c->n_particles;
+  const long long nbin = ncell;
+  const long long scan_blocks = (nbin + 1 + 8191) / 8192;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  L.f = take(2 * align_up((size_t)q * pitch * ts));
+  L.F = take((size_t)d * pitch * ts);
+  L.red = take(sizeof(double) * RED_SCRATCH);
+  L.err = take(sizeof(unsigned));
+  L.out = take(sizeof(double) * 8);
+  L.X = take(2 * align_up(sizeof(double) * d * np));
+  L.U = take(2 * align_up(sizeof(double) * d * np));
+  L.rad = take(sizeof(double) * np);
+  L.mass = take(sizeof(double) * np);
+  L.Ap = take(sizeof(double) * np);
+  L.buoy = take(sizeof(double) * np);
+  L.g = take(sizeof(double) * d * np);
+  L.Fc = take(sizeof(double) * d * np);
+  L.key = take(sizeof(unsigned) * np);
+  L.rank = take(sizeof(unsigned) * np);
+  L.perm = take(sizeof(unsigned) * np);
+  L.bin = take(sizeof(unsigned) * (nbin + 1));
+  L.bsum = take(sizeof(unsigned) * scan_blocks);
+  L.total = off;
+  return L;
+}
+
+
+#define CK(expr)                                   \
+  do {                                             \
+    cudaError_t e_ = (expr);                       \
+    if (e_ != cudaSuccess) return PIBM_ECUDA;      \
+  } while (0)
+
+int enqueue_step(pibm_t* h, cudaStream_t st) {
+  State& s = h->s;
+  int nk = 0;
+  CK(launch_bin(s, st, &nk));
+  CK(launch_couple(s, st, &nk));
+  CK(launch_collide_stream(s, st));
+  nk += 1;
+  s.cur ^= 1;
+  h->kernels_per_step = nk;
+  return PIBM_OK;
+}
+
+int build_graph(pibm_t* h, int parity) {
+  // Capture two steps starting from buffer parity `parity`; after two steps the
+  // buffers are back where they started, so the graph can be replayed.
+  cudaGraph_t g = nullptr;
+  int saved = h->s.cur;
+  h->s.cur = parity;
+  if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    h->s.cur = saved;
+    return PIBM_ECUDA;
+  }
+  int rc = enqueue_step(h, h->cap);
+  if (rc == PIBM_OK) rc = enqueue_step(h, h->cap);
+  cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+  h->s.cur = saved;
+  if (rc != PIBM_OK || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return PIBM_ECUDA;
+  }
+  e = cudaGraphInstantiate(&h->graph[parity], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h->graph[parity] = nullptr;
+    cudaGetLastError();
+    return PIBM_ECUDA;
+  }
+  return PIBM_OK;
+}
+
+int health(pibm_t* h) {
+  unsigned err = 0;
+  CK(cudaMemcpyAsync(&err, h->s.err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (err & (ERR_FLUID_NONFINITE | ERR_PARTICLE_NONFINITE)) return PIBM_EUNSTABLE;
+  if (err & ERR_ESCAPED) return PIBM_EESCAPED;
+  return PIBM_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+const char* pibm_strerror(int st) {
+  switch (st) {
+    case PIBM_OK: return "ok";
+    case PIBM_EINVAL: return "invalid argument or configuration";
+    case PIBM_ENOMEM: return "workspace too small or allocation failed";
+    case PIBM_ECUDA: return "CUDA call failed";
+    case PIBM_EUNSTABLE: return "non-finite fluid or particle state";
+    case PIBM_EESCAPED: return "a particle crossed a wall";
+    case PIBM_ENOTSUP: return "configuration not supported by this build";
+    default: return "unknown status";
+  }
+}
+
+int pibm_workspace_bytes(const pibm_config* cfg, size_t* bytes) {
+  int rc = validate(cfg);
+  if (rc != PIBM_OK) return rc;
+  if (!bytes) return PIBM_EINVAL;
+  *bytes = layout(cfg).total;
+  return PIBM_OK;
+}
+
+int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes, void* stream,
+                pibm_t** out) {
+  if (!out) return PIBM_EINVAL;
+  *out = nullptr;
+  int rc = validate(cfg);
+  if (rc != PIBM_OK) return rc;
+  const Layout L = layout(cfg);
+  if (workspace && (workspace_bytes < L.total || ((uintptr_t)workspace % ALIGN) != 0))
+    return PIBM_ENOMEM;
+
+  pibm_t* h = new (std::nothrow) pibm_t();
+  if (!h) return PIBM_ENOMEM;
+  memset(h, 0, sizeof(*h));
+  cudaGetDevice(&h->device);
+  h->stream = (cudaStream_t)stream;
+  if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    delete h;
+    return PIBM_ECUDA;
+  }
+  if (workspace) {
+    h->ws = workspace;
+    h->owns_ws = 0;
+  } else {
+    if (cudaMalloc(&h->ws, L.total) != cudaSuccess) {
+      cudaGetLastError();
+      cudaStreamDestroy(h->cap);
+      delete h;
+      return PIBM_ENOMEM;
+    }
+    h->owns_ws = 1;
+  }
+  h->ws_bytes = L.total;
+  char* base = (char*)h->ws;
+
+  State& s = h->s;
+  const int q = cfg->lattice, d = dims_of(q);
+  s.geo.q = q;
+  s.geo.d = d;
+  for (int k = 0; k < 3; ++k) {
+    s.geo.n[k] = (int)cfg->n[k];
+    s.geo.periodic[k] = (k < d) ? (cfg->boundary[k] == PIBM_PERIODIC) : 1;
+  }
+  s.geo.ncell = cfg->n[0] * cfg->n[1] * cfg->n[2];
+  s.geo.pitch = (s.geo.ncell + 63) / 64 * 64;
+  s.phy.tau = cfg->tau;
+  s.phy.omega = 1.0 / cfg->tau;
+  s.phy.cF = 1.0 - 0.5 / cfg->tau;
+  for (int k = 0; k < 3; ++k) s.phy.gravity[k] = k < d ? cfg->gravity[k] : 0.0;
+  s.phy.kn = cfg->dem_kn;
+  {
+    const double lne = log(cfg->dem_restitution);
+    s.phy.beta = -lne / sqrt(M_PI * M_PI + lne * lne);
+  }
+  s.phy.width = cfg->delta_width;
+  s.phy.implicit_drag = cfg->coupling == PIBM_IMPLICIT;
+  s.precision = cfg->precision;
+  s.deterministic = cfg->deterministic ? 1 : 0;
+  const size_t ts = cfg->precision == PIBM_FP64 ? 8 : 4;
+  const size_t fbuf = align_up((size_t)q * s.geo.pitch * ts);
+  s.f[0] = base + L.f;
+  s.f[1] = base + L.f + fbuf;
+  s.F = base + L.F;
+  s.red = (double*)(base + L.red);
+  s.err = (unsigned*)(base + L.err);
+  h->out_dev = (double*)(base + L.out);
+  const long long np = cfg->n_particles;
+  Particles& P = s.p;
+  P.np = np;
+  const size_t xb = align_up(sizeof(double) * d * np);
+  P.X[0] = (double*)(base + L.X);
+  P.X[1] = (double*)(base + L.X + xb);
+  P.U[0] = (double*)(base + L.U);
+  P.U[1] = (double*)(base + L.U + xb);
+  P.rad = (double*)(base + L.rad);
+  P.mass = (double*)(base + L.mass);
+  P.Ap = (double*)(base + L.Ap);
+  P.buoy = (double*)(base + L.buoy);
+  P.g = (double*)(base + L.g);
+  P.Fc = (double*)(base + L.Fc);
+  P.key = (unsigned*)(base + L.key);
+  P.rank = (unsigned*)(base + L.rank);
+  P.perm = (unsigned*)(base + L.perm);
+  P.bin_cnt = (unsigned*)(base + L.bin);
+  P.block_sums = (unsigned*)(base + L.bsum);
+  P.nbin = s.geo.ncell;
+  P.scan_blocks = (int)((P.nbin + 1 + 8191) / 8192);
+  s.cur = 0;
+
+  cudaStream_t st = h->stream;
+  auto fail = [&](int code) {
+    pibm_destroy(h);
+    return code;
+  };
+  // force field and health word start at zero
+  if (cudaMemsetAsync(s.F, 0, (size_t)d * s.geo.pitch * ts, st) != cudaSuccess ||
+      cudaMemsetAsync(s.err, 0, sizeof(unsigned), st) != cudaSuccess)
+    return fail(PIBM_ECUDA);
+
+  // populations: store f*_a(y) = f0_a(y + e_a), or f0_opp(a)(y) across a wall,
+  // so that the first pull reproduces f0 (streaming is a permutation of slots)
+  if (cfg->f0) {
+    std::vector<double> plane((size_t)s.geo.ncell);
+    double* stage = (double*)s.f[1];  // the partner buffer is free before the first step
+    int e[19][3];
+    for (int a = 0; a < q; ++a)
+      for (int k = 0; k < 3; ++k)
+        e[a][k] = q == 9 ? Lattice<9>::e(a, k) : (q == 15 ? Lattice<15>::e(a, k) : Lattice<19>::e(a, k));
+    const int n0 = s.geo.n[0], n1 = s.geo.n[1], n2 = s.geo.n[2];
+    for (int a = 0; a < q; ++a) {
+      const int b = opp(a);
+      for (int z = 0; z < n2; ++z)
+        for (int y = 0; y < n1; ++y)
+          for (int x = 0; x < n0; ++x) {
+            int t[3] = {x + e[a][0], y + e[a][1], z + e[a][2]};
+            bool wall = false;
+            for (int k = 0; k < 3; ++k) {
+              if (t[k] < 0 || t[k] >= s.geo.n[k]) {
+                if (s.geo.periodic[k]) t[k] = (t[k] + s.geo.n[k]) % s.geo.n[k];
+                else wall = true;
+              }
+            }
+            const long long c = x + (long long)n0 * (y + (long long)n1 * z);
+            const long long tc = t[0] + (long long)n0 * (t[1] + (long long)n1 * t[2]);
+            plane[c] = wall ? cfg->f0[(size_t)b * s.geo.ncell + c]
+                            : cfg->f0[(size_t)a * s.geo.ncell + tc];
+          }
+      if (cudaMemcpyAsync(stage, plane.data(), sizeof(double) * s.geo.ncell,
+                          cudaMemcpyHostToDevice, st) != cudaSuccess ||
+          launch_store_plane(s, a, stage, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        return fail(PIBM_ECUDA);
+    }
+  } else {
+    for (int a = 0; a < q; ++a)
+      if (launch_store_plane(s, a, nullptr, st) != cudaSuccess) return fail(PIBM_ECUDA);
+  }
+
+  if (np > 0) {
+    // AoS -> SoA on the host, then upload
+    std::vector<double> soa((size_t)d * np);
+    for (int k = 0; k < d; ++k)
+      for (long long p = 0; p < np; ++p) soa[(size_t)k * np + p] = cfg->x0[p * d + k];
+    if (cudaMemcpyAsync(P.X[0], soa.data(), sizeof(double) * d * np, cudaMemcpyHostToDevice,
+                        st) != cudaSuccess)
+      return fail(PIBM_ECUDA);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return fail(PIBM_ECUDA);
+    for (int k = 0; k < d; ++k)
+      for (long long p = 0; p < np; ++p)
+        soa[(size_t)k * np + p] = cfg->u0 ? cfg->u0[p * d + k] : 0.0;
+    if (cudaMemcpyAsync(P.U[0], soa.data(), sizeof(double) * d * np, cudaMemcpyHostToDevice,
+                        st) != cudaSuccess ||
+        cudaMemcpyAsync(P.rad, cfg->diameter, sizeof(double) * np, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(P.buoy, cfg->density_ratio, sizeof(double) * np, cudaMemcpyHostToDevice,
+                        st) != cudaSuccess ||
+        cudaMemsetAsync(P.g, 0, sizeof(double) * d * np, st) != cudaSuccess ||
+        cudaMemsetAsync(P.Fc, 0, sizeof(double) * d * np, st) != cudaSuccess ||
+        launch_particle_init(s, st) != cudaSuccess)
+      return fail(PIBM_ECUDA);
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) return fail(PIBM_ECUDA);
+  h->kernels_per_step = np > 0 ? (s.deterministic ? 9 : 8) : 1;
+  *out = h;
+  return PIBM_OK;
+}
+
+int pibm_step(pibm_t* h, int64_t nsteps) {
+  if (!h || nsteps < 0) return PIBM_EINVAL;
+  DeviceGuard guard(h->device);
+  while (nsteps > 0) {
+    if (nsteps >= 2 && !h->graph_failed) {
+      const int par = h->s.cur;
+      if (!h->graph[par] && build_graph(h, par) != PIBM_OK) {
+        h->graph_failed = 1;
+        continue;
+      }
+      CK(cudaGraphLaunch(h->graph[par], h->stream));
+      nsteps -= 2;  // two toggles leave s.cur unchanged
+    } else {
+      int rc = enqueue_step(h, h->stream);
+      if (rc != PIBM_OK) return rc;
+      nsteps -= 1;
+    }
+  }
+  return PIBM_OK;
+}
+
+int pibm_forces(pibm_t* h, double* f_fpi, double* f_contact, int on_device) {
+  if (!h) return PIBM_EINVAL;
+  DeviceGuard guard(h->device);
+  State& s = h->s;
+  const long long np = s.p.np;
+  const int d = s.geo.d;
+  if (np > 0 && (f_fpi || f_contact)) {
+    if (on_device) {
+      CK(launch_particle_forces(s, f_fpi, f_contact, h->stream));
+    } else {
+      double* stage = (double*)s.f[1 - s.cur];  // free between steps
+      double* a = stage;
+      double* b = stage + (size_t)d * np;
+      size_t need = sizeof(double) * 2 * d * np;
+      size_t have = align_up((size_t)s.geo.q * s.geo.pitch * (s.precision == PIBM_FP64 ? 8 : 4));
+      if (need > have) return PIBM_ENOMEM;
+      CK(launch_particle_forces(s, f_fpi ? a : nullptr, f_contact ? b : nullptr, h->stream));
+      if (f_fpi)
+        CK(cudaMemcpyAsync(f_fpi, a, sizeof(double) * d * np, cudaMemcpyDeviceToHost, h->stream));
+      if (f_contact)
+        CK(cudaMemcpyAsync(f_contact, b, sizeof(double) * d * np, cudaMemcpyDeviceToHost,
+                           h->stream));
+    }
+  }
+  return health(h);
+}
+
+int pibm_read_fields(pibm_t* h, unsigned mask, void* const* dst, int on_device) {
+  if (!h || (mask && !dst)) return PIBM_EINVAL;
+  if (mask >> PIBM_NFIELDS) return PIBM_EINVAL;
+  for (int k = 0; k < PIBM_NFIELDS; ++k)
+    if ((mask >> k & 1u) && !dst[k]) return PIBM_EINVAL;
+  DeviceGuard guard(h->device);
+  State& s = h->s;
+  const long long nc = s.geo.ncell, np = s.p.np;
+  const int d = s.geo.d, q = s.geo.q;
+  cudaStream_t st = h->stream;
+  double* stage = (double*)s.f[1 - s.cur];  // partner buffer holds >= ncell doubles
+  auto plane_out = [&](double* dstp, auto launch) -> int {
+    if (on_device) {
+      CK(launch(dstp));
+    } else {
+      CK(launch(stage));
+      CK(cudaMemcpyAsync(dstp, stage, sizeof(double) * nc, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    }
+    return PIBM_OK;
+  };
+  int rc;
+  if (mask & PIBM_FIELD_RHO) {
+    rc = plane_out((double*)dst[0], [&](double* o) { return launch_read_moment(s, 0, o, st); });
+    if (rc) return rc;
+  }
+  if (mask & PIBM_FIELD_J) {
+    for (int k = 0; k < d; ++k) {
+      rc = plane_out((double*)dst[1] + (size_t)k * nc,
+                     [&](double* o) { return launch_read_moment(s, k + 1, o, st); });
+      if (rc) return rc;
+    }
+  }
+  if (mask & PIBM_FIELD_POP) {
+    for (int a = 0; a < q; ++a) {
+      rc = plane_out((double*)dst[2] + (size_t)a * nc,
+                     [&](double* o) { return launch_read_pop_plane(s, a, o, st); });
+      if (rc) return rc;
+    }
+  }
+  for (int f = 0; f < 2; ++f) {
+    const unsigned bit = f == 0 ? PIBM_FIELD_X : PIBM_FIELD_U;
+    if (!(mask & bit) || np == 0) continue;
+    const double* src = f == 0 ? s.p.X[s.cur] : s.p.U[s.cur];
+    double* o = (double*)dst[f == 0 ? 3 : 4];
+    if (on_device) {
+      CK(launch_interleave(s, src, o, st));
+    } else {
+      std::vector<double> soa((size_t)d * np);
+      CK(cudaMemcpyAsync(soa.data(), src, sizeof(double) * d * np, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (long long p = 0; p < np; ++p)
+        for (int k = 0; k < d; ++k) o[p * d + k] = soa[(size_t)k * np + p];
+    }
+  }
+  return health(h);
+}
+
+int pibm_invariants(pibm_t* h, double* out) {
+  if (!h || !out) return PIBM_EINVAL;
+  DeviceGuard guard(h->device);
+  State& s = h->s;
+  const int d = s.geo.d;
+  CK(launch_invariants(s, h->out_dev, h->stream));
+  CK(launch_particle_momentum(s, h->out_dev + 1 + d, h->stream));
+  CK(cudaMemcpyAsync(out, h->out_dev, sizeof(double) * (1 + 2 * d), cudaMemcpyDeviceToHost,
+                     h->stream));
+  return health(h);
+}
+
+int pibm_status(pibm_t* h) {
+  if (!h) return PIBM_EINVAL;
+  DeviceGuard guard(h->device);
+  return health(h);
+}
+
+int pibm_kernels_per_step(pibm_t* h) { return h ? h->kernels_per_step : 0; }
+
+int pibm_profile_steps(pibm_t* h, int64_t nsteps, double* phase_ms) {
+  if (!h || nsteps < 0 || !phase_ms) return PIBM_EINVAL;
+  DeviceGuard guard(h->device);
+  for (int k = 0; k < 4; ++k) phase_ms[k] = 0.0;
+  if (nsteps == 0) return health(h);
+  State& s = h->s;
+  cudaStream_t st = h->stream;
+  std::vector<cudaEvent_t> ev((size_t)3 * nsteps + 1, nullptr);
+  int rc = PIBM_OK;
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) rc = PIBM_ECUDA;
+  if (rc == PIBM_OK) {
+    int nk = 0;
+    if (cudaEventRecord(ev[0], st) != cudaSuccess) rc = PIBM_ECUDA;
+    for (int64_t i = 0; i < nsteps && rc == PIBM_OK; ++i) {
+      nk = 0;
+      if (launch_bin(s, st, &nk) != cudaSuccess ||
+          cudaEventRecord(ev[3 * i + 1], st) != cudaSuccess ||
+          launch_couple(s, st, &nk) != cudaSuccess ||
+          cudaEventRecord(ev[3 * i + 2], st) != cudaSuccess ||
+          launch_collide_stream(s, st) != cudaSuccess ||
+          cudaEventRecord(ev[3 * i + 3], st) != cudaSuccess) {
+        rc = PIBM_ECUDA;
+        break;
+      }
+      s.cur ^= 1;
+    }
+    if (rc == PIBM_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = PIBM_ECUDA;
+    for (int64_t i = 0; i < nsteps && rc == PIBM_OK; ++i) {
+      float t[3];
+      for (int k = 0; k < 3; ++k) {
+        if (cudaEventElapsedTime(&t[k], ev[3 * i + k], ev[3 * i + k + 1]) != cudaSuccess) {
+          rc = PIBM_ECUDA;
+          t[k] = 0.f;
+        }
+        phase_ms[k] += t[k];
+      }
+    }
+    float tot = 0.f;
+    if (rc == PIBM_OK && cudaEventElapsedTime(&tot, ev[0], ev[3 * nsteps]) != cudaSuccess)
+      rc = PIBM_ECUDA;
+    phase_ms[3] = tot;
+  }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  if (rc != PIBM_OK) return rc;
+  return health(h);
+}
+
+void pibm_destroy(pibm_t* h) {
+  if (!h) return;
+  DeviceGuard guard(h->device);
+  cudaStreamSynchronize(h->stream);
+  for (int i = 0; i < 2; ++i)
+    if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->owns_ws && h->ws) cudaFree(h->ws);
+  delete h;
+}
+
+}  // extern "C"

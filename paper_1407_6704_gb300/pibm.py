@@ -1,0 +1,177 @@
+"""Python binding of the PIBM C ABI: argument marshalling around ``libpibm.so``.
+
+PyTorch provides the device workspace (one uint8 tensor) and the stream; every
+computation runs in the CUDA library. Arrays handed to or returned from this
+module are NumPy FP64 with the layouts of ``include/pibm.h``.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (FIELD_J, FIELD_POP, FIELD_RHO, FIELD_U, FIELD_X, PibmConfig, check)
+
+_LATTICES = {"d2q9": 9, "d3q15": 15, "d3q19": 19, 9: 9, 15: 15, 19: 19}
+_PRECISION = {"fp64": _lib.PIBM_FP64, "fp32": _lib.PIBM_FP32}
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a, shape=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    return a.reshape(shape) if shape is not None else a
+
+
+class Pibm:
+    """One coupled LBM-PIBM-DEM simulation living on one GPU.
+
+    lattice: "d2q9" | "d3q15" | "d3q19"; n: extents (2 or 3 ints);
+    periodic: per-axis flags (False = walls at 0 and n); tau: BGK relaxation time;
+    gravity: particle acceleration; delta_width: 2 or 4; implicit: drag coupling;
+    precision: "fp64" | "fp32"; deterministic: ordered spreading;
+    x0, u0 (n_particles, d), diameter, density_ratio (n_particles,);
+    f0: optional (q, ...) post-stream populations of step 0.
+    """
+
+    def __init__(self, lattice, n, periodic, tau, gravity=None, delta_width=2, implicit=True,
+                 precision="fp64", deterministic=False, kn=1e-2, restitution=0.9, x0=None,
+                 u0=None, diameter=None, density_ratio=None, f0=None, device=None, stream=None):
+        import torch
+
+        self._torch = torch
+        L = _lib.load()
+        self.q = _LATTICES[lattice]
+        self.d = 2 if self.q == 9 else 3
+        n = list(n) + [1] * (3 - len(n))
+        self.n = n
+        self.shape = (n[1], n[0]) if self.d == 2 else (n[2], n[1], n[0])
+        self.ncell = n[0] * n[1] * n[2]
+        per = list(periodic) + [1] * (3 - len(periodic))
+        np_ = 0 if x0 is None else int(np.asarray(x0).shape[0])
+        self.np = np_
+        self._x0 = _f64(x0, (np_, self.d)) if np_ else None
+        self._u0 = _f64(u0, (np_, self.d)) if (np_ and u0 is not None) else None
+        self._dia = _f64(diameter, (np_,)) if np_ else None
+        self._rr = _f64(density_ratio, (np_,)) if np_ else None
+        self._f0 = _f64(f0, (self.q, self.ncell)) if f0 is not None else None
+        grav = list(gravity) if gravity is not None else [0.0] * self.d
+        grav = (grav + [0.0, 0.0, 0.0])[:3]
+        self.cfg = PibmConfig(
+            self.q, (ctypes.c_int64 * 3)(*n),
+            (ctypes.c_int * 3)(*[_lib.PIBM_PERIODIC if p else _lib.PIBM_WALL for p in per]),
+            float(tau), (ctypes.c_double * 3)(*grav), int(delta_width),
+            _lib.PIBM_IMPLICIT if implicit else _lib.PIBM_EXPLICIT, _PRECISION[precision],
+            int(bool(deterministic)), float(kn), float(restitution), np_,
+            _dptr(self._x0), _dptr(self._u0), _dptr(self._dia), _dptr(self._rr),
+            _dptr(self._f0))
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
+            else torch.device(device)
+        nbytes = ctypes.c_size_t()
+        check(L.pibm_workspace_bytes(ctypes.byref(self.cfg), ctypes.byref(nbytes)),
+              "pibm_workspace_bytes")
+        self.workspace_bytes = nbytes.value
+        with torch.cuda.device(self.device):
+            self._ws = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=self.device)
+            base = self._ws.data_ptr()
+            self._ws_ptr = (base + 255) // 256 * 256
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            h = ctypes.c_void_p()
+            check(L.pibm_create(ctypes.byref(self.cfg), ctypes.c_void_p(self._ws_ptr),
+                                nbytes.value, ctypes.c_void_p(self.stream.cuda_stream),
+                                ctypes.byref(h)), "pibm_create")
+        self._h = h
+        self._L = L
+
+    # --- stepping ----------------------------------------------------------------
+    def step(self, nsteps=1):
+        check(self._L.pibm_step(self._h, int(nsteps)), "pibm_step")
+
+    def profile_steps(self, nsteps):
+        """Run nsteps steps phase by phase; summed device ms per phase:
+        {'bin', 'particles', 'collide_stream', 'total'}."""
+        out = np.zeros(4)
+        check(self._L.pibm_profile_steps(self._h, int(nsteps), _dptr(out)), "pibm_profile_steps")
+        return dict(zip(("bin", "particles", "collide_stream", "total"), out.tolist()))
+
+    def status(self):
+        return self._L.pibm_status(self._h)
+
+    @property
+    def kernels_per_step(self):
+        return self._L.pibm_kernels_per_step(self._h)
+
+    # --- read-back -----------------------------------------------------------------
+    def forces(self):
+        """(f_fpi, f_contact), each (n_particles, d) FP64 on the host."""
+        ffpi = np.zeros((self.np, self.d))
+        fc = np.zeros((self.np, self.d))
+        if self.np:
+            check(self._L.pibm_forces(self._h, ffpi.ctypes.data_as(ctypes.c_void_p),
+                                      fc.ctypes.data_as(ctypes.c_void_p), 0), "pibm_forces")
+        return ffpi, fc
+
+    def read(self, *names):
+        """Host copies of the requested fields: 'rho', 'j', 'pop', 'x', 'u'."""
+        bits = {"rho": (0, FIELD_RHO, (self.ncell,)), "j": (1, FIELD_J, (self.d, self.ncell)),
+                "pop": (2, FIELD_POP, (self.q, self.ncell)), "x": (3, FIELD_X, (self.np, self.d)),
+                "u": (4, FIELD_U, (self.np, self.d))}
+        out = {}
+        dst = (ctypes.c_void_p * _lib.NFIELDS)()
+        mask = 0
+        for nm in names:
+            k, bit, shp = bits[nm]
+            arr = np.zeros(shp)
+            out[nm] = arr
+            dst[k] = arr.ctypes.data_as(ctypes.c_void_p).value if arr.size else 1
+            mask |= bit if arr.size else 0
+        check(self._L.pibm_read_fields(self._h, mask, dst, 0), "pibm_read_fields")
+        res = {}
+        for nm, arr in out.items():
+            if nm == "rho":
+                res[nm] = arr.reshape(self.shape)
+            elif nm in ("j", "pop"):
+                res[nm] = arr.reshape((arr.shape[0],) + self.shape)
+            else:
+                res[nm] = arr
+        return res
+
+    def invariants(self):
+        """(total mass, fluid momentum (d,), particle momentum (d,))."""
+        out = np.zeros(1 + 2 * self.d)
+        check(self._L.pibm_invariants(self._h, _dptr(out)), "pibm_invariants")
+        return out[0], out[1:1 + self.d].copy(), out[1 + self.d:].copy()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.pibm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # --- presets ---------------------------------------------------------------------
+    @classmethod
+    def from_workload(cls, w, precision="fp64", n_particles=None, particles=None, f0=None,
+                      **kw):
+        """Build a simulation from an ``inputs.Workload`` preset (seeded particles)."""
+        from .inputs import workload_particles
+        X, dia, rr = particles if particles is not None else workload_particles(w, n_particles)
+        lat = {9: "d2q9", 15: "d3q15", 19: "d3q19"}[w.q]
+        return cls(lat, w.n, w.periodic, w.tau, gravity=w.gravity, delta_width=w.delta_width,
+                   precision=precision, kn=w.kn, restitution=w.restitution, x0=X, diameter=dia,
+                   density_ratio=rr, f0=f0, **kw)
