@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Benchmark of the coupled LBM-PIBM-DEM step on the 2D sedimentation workload
+(D2Q9 2048 x 2048 with walls, tau 0.6, 500,000 particles with diameters uniform in
+[0.3, 0.8] lu and density ratio 2.5 in the top 60 %, 4-point delta).
+
+Prints one JSON line. ``value`` is whole-job MLUPS (lattice-cell updates per
+second, coupled step, all ranks); particle updates per second ride along. Inputs
+are resident in HBM when the timed region starts and the two population buffers
+(2 x 151 MB in FP32, 2 x 302 MB in FP64) exceed the 129 MB L2, so no flush is
+needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--impl reference times the FP64 CPU oracle (test infrastructure) on a bounded
+sample of the same workload on the host cores.
+"""
+import argparse
+import glob
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+# FP64 FMA throughput measured on this machine's GB300 (CUDA-core FMA chains):
+# 1.19 TFLOP/s; nominal 1.25 TFLOP/s.
+FP64_PEAK_TFLOPS = 1.19
+WORKLOAD_DESC = ("2D sedimentation: D2Q9 2048x2048 walls, tau 0.6, 500k particles "
+                 "d~U[0.3,0.8] lu, rho_p/rho_f 2.5, top 60%, gravity 1e-5, 4-point delta, "
+                 "linear spring-dashpot kn 1e-2 e 0.9")
+
+
+def _peaks():
+    try:
+        with open(PEAKS_FILE) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _src_hash():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1407_6704_gb300", "csrc", "*"))):
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel, workload):
+    """DRAM bytes per launch from a committed ncu summary, only if the kernel
+    sources are unchanged since it was captured."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            t = json.load(fh)
+        ent = t.get(kernel)
+        if ent and ent.get("workload") == workload and ent.get("source_sha") == _src_hash():
+            return float(ent["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id):
+        self.dev = device_id
+        self.proc = None
+        self.tmp = None
+
+    def __enter__(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.dev)], stdout=self.tmp, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.tmp:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.tmp.flush()
+        with open(self.tmp.name) as fh:
+            rows = [r.strip().split(",") for r in fh if r.strip()]
+        os.unlink(self.tmp.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+                for nm, v in zip(names, r[4:8]):
+                    if v.strip().lower() in ("active", "1"):
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def collide_bytes_per_cell(q, precision):
+    return 2 * q * (8 if precision == "fp64" else 4)
+
+
+def particle_bytes(d):
+    # read X, U, d_p and write X, U in FP64: (4 d + 1) * 8 bytes per particle
+    return (4 * d + 1) * 8
+
+
+def collide_flops_per_cell_fp64(q):
+    # FP64 operations of the fused collision (counted from the kernel's arithmetic:
+    # moments, velocity, per-pair relaxation); used for the ALU roofline of FP64
+    return {9: 91, 15: 150, 19: 185}[q]
+
+
+def run_gpu(args, rank, world):
+    import torch
+    from paper_1407_6704_gb300 import build
+    from paper_1407_6704_gb300.inputs import preset, workload_particles
+    from paper_1407_6704_gb300.pibm import Pibm
+
+    build.build()
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = preset(args.workload)
+    # replicas: each rank sedimentes its own independent instance
+    w.seed = w.seed + 1000 * rank
+    X, dia, rr = workload_particles(w)
+    peak_gbs, peak_src = _peaks()
+    props = torch.cuda.get_device_properties(local)
+    dev_id = str(getattr(props, "uuid", local))
+    if dev_id and not dev_id.startswith("GPU-") and "-" in dev_id:
+        dev_id = "GPU-" + dev_id
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    results = {}
+    clocks = None
+    for prec in [args.precision] + [p for p in ("fp64", "fp32") if p != args.precision]:
+        sim = Pibm.from_workload(w, precision=prec, particles=(X, dia, rr))
+        sim.step(args.warmup)
+        barrier()
+        if prec == args.precision:
+            with ClockSampler(dev_id) as cs:
+                ph = sim.profile_steps(args.steps)
+            clocks = cs.summary()
+        else:
+            ph = sim.profile_steps(args.steps)
+        barrier()
+        ms_step = max_over_ranks(ph["total"] / args.steps)
+        # graph-replayed steps (the default pibm_step path)
+        stream = sim.stream
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        sim.step(args.steps)
+        e1.record(stream)
+        barrier()
+        ms_graph = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+        st = sim.status()
+        kps = sim.kernels_per_step
+        sim.close()
+        results[prec] = dict(ms=ms_step, ms_graph=ms_graph, phases={k: v / args.steps for k, v
+                                                                   in ph.items()},
+                             status=st, kps=kps)
+        if not args.both:
+            break
+
+    # end to end through the public API with host buffers: create (host -> device
+    # upload of the particle set; populations start at rest on the device), K steps,
+    # read positions and velocities back to the host
+    prec = args.precision
+    barrier()
+    t0 = time.perf_counter()
+    sim = Pibm.from_workload(w, precision=prec, particles=(X, dia, rr))
+    sim.step(args.steps)
+    out = sim.read("x", "u")
+    sim.close()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    h2d = X.nbytes + dia.nbytes + rr.nbytes
+    d2h = out["x"].nbytes + out["u"].nbytes
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return None
+
+    r = results[prec]
+    cells = w.ncell
+    mlups = world * cells / (r["ms"] * 1e-3) / 1e6
+    pups = world * w.n_particles / (r["ms"] * 1e-3)
+    # dominant kernel roofline
+    ph = r["phases"]
+    algo_cell = collide_bytes_per_cell(w.q, prec)
+    kern = {
+        "collide_stream": dict(kernel="k_collide_stream", ms=ph["collide_stream"],
+                               bytes=cells * algo_cell),
+        "couple": dict(kernel="k_couple", ms=ph["couple"],
+                       bytes=w.n_particles * particle_bytes(w.d)),
+        "contacts": dict(kernel="k_contacts", ms=ph["contacts"], bytes=None),
+        "bin": dict(kernel="k_bin_* + k_scan_*", ms=ph["bin"], bytes=None),
+    }
+    for k, v in kern.items():
+        v["share"] = v["ms"] / max(ph["total"], 1e-12)
+        if v["bytes"]:
+            v["achieved_gbs"] = v["bytes"] / (v["ms"] * 1e-3) / 1e9
+            v["frac_hbm"] = v["achieved_gbs"] / peak_gbs
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    if prec == "fp64" and dom == "collide_stream":
+        flops = cells * collide_flops_per_cell_fp64(w.q)
+        ach = flops / (ph["collide_stream"] * 1e-3) / 1e12
+        roof = {"kernel": "k_collide_stream", "bound": "alu", "achieved": ach,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": _traffic("k_collide_stream", f"{args.workload}-{prec}"),
+                "peak_source": "measured FP64 FMA rate"}
+    else:
+        kk = dom if kern[dom]["bytes"] else "collide_stream"
+        ach = kern[kk]["achieved_gbs"]
+        name = kern[kk]["kernel"]
+        roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak_gbs,
+                "unit": "GB/s", "frac": ach / peak_gbs,
+                "traffic": _traffic(name, f"{args.workload}-{prec}"),
+                "peak_source": f"{peak_src} copy bandwidth"}
+    step_bytes = cells * algo_cell + w.n_particles * particle_bytes(w.d)
+    step_roof = {"algorithmic_bytes": step_bytes,
+                 "achieved_gbs": step_bytes / (r["ms"] * 1e-3) / 1e9}
+    step_roof["frac"] = step_roof["achieved_gbs"] / peak_gbs
+
+    line = {
+        "metric": "coupled-step MLUPS (lattice updates/s of the full LBM-PIBM-DEM step)",
+        "value": mlups,
+        "unit": "MLUPS",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": r["ms"],
+        "ms_per_step_graph": r["ms_graph"],
+        "particle_updates_per_s": pups,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp64": "f64"}[prec],
+        "data": "synthetic (seeded uniform non-overlapping particles, fluid at rest)",
+        "config": {"workload": WORKLOAD_DESC, "lattice": "D2Q9", "n": list(w.n),
+                   "particles": w.n_particles, "precision": prec,
+                   "particle_state": "f64", "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (population buffers 2x151 MB f32 / 2x302 MB f64)"},
+        "phases_ms_per_step": ph,
+        "kernels": kern,
+        "roofline": roof,
+        "step_roofline": step_roof,
+        "clocks": clocks,
+        "e2e": {"value": world * cells * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+                "seconds": e2e_s, "h2d_bytes_per_step": h2d / args.steps,
+                "d2h_bytes_per_step": d2h / args.steps,
+                "note": "create from host arrays + K steps + read X, U to host"},
+        "gpu_launches": args.steps * r["kps"],
+        "status": r["status"],
+    }
+    for p, rr_ in results.items():
+        if p == prec:
+            continue
+        line[p] = {"ms_per_step": rr_["ms"], "ms_per_step_graph": rr_["ms_graph"],
+                   "value": world * cells / (rr_["ms"] * 1e-3) / 1e6, "unit": "MLUPS",
+                   "phases_ms_per_step": rr_["phases"], "status": rr_["status"]}
+        if p == "fp64":
+            fl = cells * collide_flops_per_cell_fp64(w.q)
+            a = fl / (rr_["phases"]["collide_stream"] * 1e-3) / 1e12
+            line[p]["collide_roofline"] = {"bound": "alu", "achieved": a,
+                                           "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                           "frac": a / FP64_PEAK_TFLOPS}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, w)
+    if dist is not None:
+        dist.destroy_process_group()
+    return line
+
+
+def cpu_sample(w, side=256):
+    """A side x side patch of the workload with the same particle density."""
+    from paper_1407_6704_gb300.inputs import sample_particles
+    frac = (side * side) / float(w.ncell)
+    npart = int(round(w.n_particles * frac))
+    X, dia, rr = sample_particles((side, side), npart, w.diameter, w.density_ratio, w.band,
+                                  w.seed)
+    return (side, side), X, dia, rr
+
+
+def cpu_baseline(args, w, budget_s=15.0):
+    from oracle.oracle import Oracle
+    n, X, dia, rr = cpu_sample(w)
+    o = Oracle(w.q, n, w.periodic, w.tau, delta_width=w.delta_width, gravity=w.gravity,
+               kn=w.kn, restitution=w.restitution, x0=X, diameter=dia, density_ratio=rr)
+    o.step(1)
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < budget_s:
+        o.step(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    cells = n[0] * n[1]
+    return {"value": cells * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{n[0]}x{n[1]} patch of the workload with the same particle density "
+                      f"({len(X)} particles), {steps} steps, {dt:.1f} s, single thread",
+            "particle_updates_per_s": len(X) * steps / dt}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from paper_1407_6704_gb300.inputs import preset
+    w = preset(args.workload)
+    from oracle.oracle import Oracle
+    n, X, dia, rr = cpu_sample(w)
+    o = Oracle(w.q, n, w.periodic, w.tau, delta_width=w.delta_width, gravity=w.gravity,
+               kn=w.kn, restitution=w.restitution, x0=X, diameter=dia, density_ratio=rr)
+    o.step(max(args.warmup, 0))
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    cells = n[0] * n[1]
+    v = cells * args.steps / dt / 1e6
+    return {"impl": "reference", "metric": "coupled-step MLUPS (lattice updates/s of the full "
+            "LBM-PIBM-DEM step)", "value": v, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD_DESC, "lattice": "D2Q9",
+                                            "n": list(n), "particles": len(X)},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": f"{n[0]}x{n[1]} patch with the workload's particle "
+                                       f"density ({len(X)} particles), single thread"},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--both", type=int, default=1, help="also time the other precision")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.gpus != world and world > 1:
+        ap.error("--gpus must equal WORLD_SIZE under torchrun")
+    line = run_reference(args, rank, world) if args.impl == "reference" else \
+        run_gpu(args, rank, world)
+    if line is not None and rank == 0:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

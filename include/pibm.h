@@ -156,10 +156,10 @@ int pibm_kernels_per_step(pibm_t* h);
 
 /* Advance nsteps steps like pibm_step, launched one phase at a time with CUDA
  * events between the phases, and return the summed device time of each phase
- * in milliseconds: phase_ms[0] cell-list binning, phase_ms[1] particle phase
- * (interpolation, contacts, update, spreading), phase_ms[2] fused
- * stream-collide, phase_ms[3] the whole steps (first event to last).
- * Synchronises the stream. Not part of the method; a timing aid. */
+ * in milliseconds: phase_ms[0] cell-list binning, phase_ms[1] contact forces,
+ * phase_ms[2] particle coupling (interpolation, update, spreading),
+ * phase_ms[3] fused stream-collide, phase_ms[4] the whole steps (first event to
+ * last). Synchronises the stream. Not part of the method; a timing aid. */
 int pibm_profile_steps(pibm_t* h, int64_t nsteps, double* phase_ms);
 
 /* Free the handle (and the workspace when the library allocated it). NULL is a no-op. */

@@ -33,11 +33,29 @@ constexpr size_t ALIGN = 256;
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-  size_t f, F, red, err, out, X, U, rad, mass, Ap, buoy, g, Fc, key, rank, perm, bin, bsum;
+  size_t f, F, red, err, out, X, U, rad, mass, Ap, buoy, gw, radf, xf, g, Fc, key, rank, perm, bin,
+      bsum;
   size_t total;
 };
 
 int dims_of(int lattice) { return lattice == PIBM_D2Q9 ? 2 : 3; }
+
+// Tile shape of the particle kernel: 32 x 8 cells in 2D, 16 x 8 x 4 in 3D.
+BinMap bin_map(const pibm_config* c) {
+  BinMap b;
+  const int d = dims_of(c->lattice);
+  b.T[0] = d == 2 ? TileDims<2>::TX : TileDims<3>::TX;
+  b.T[1] = d == 2 ? TileDims<2>::TY : TileDims<3>::TY;
+  b.T[2] = d == 2 ? TileDims<2>::TZ : TileDims<3>::TZ;
+  for (int k = 0; k < 3; ++k) b.nt[k] = (int)((c->n[k] + b.T[k] - 1) / b.T[k]);
+  b.tc = b.T[0] * b.T[1] * b.T[2];
+  return b;
+}
+
+long long bin_count(const pibm_config* c) {
+  BinMap b = bin_map(c);
+  return (long long)b.nt[0] * b.nt[1] * b.nt[2] * b.tc;
+}
 
 int validate(const pibm_config* c) {
   if (!c) return PIBM_EINVAL;
@@ -52,8 +70,9 @@ int validate(const pibm_config* c) {
     ncell *= c->n[k];
   }
   if (d == 2 && c->n[2] != 1) return PIBM_EINVAL;
-  // bins are cells; the cell-list scan covers up to 8192 * 8192 entries
-  if (ncell + 1 > 8192LL * 8192LL) return PIBM_ENOTSUP;
+  // bins are cells padded to whole tiles; the cell-list scan covers up to
+  // 8192 * 8192 entries
+  if (bin_count(c) + 1 > 8192LL * 8192LL) return PIBM_ENOTSUP;
   if (!(c->tau > 0.5) || !isfinite(c->tau)) return PIBM_EINVAL;
   if (c->delta_width != 2 && c->delta_width != 4) return PIBM_EINVAL;
   if (c->coupling != PIBM_IMPLICIT && c->coupling != PIBM_EXPLICIT) return PIBM_EINVAL;
@@ -93,7 +112,7 @@ Layout layout(const pibm_config* c) {
   const long long pitch = (ncell + 63) / 64 * 64;
   const size_t ts = c->precision == PIBM_FP64 ? 8 : 4;
   const long long np = c->n_particles;
-  const long long nbin = ncell;
+  const long long nbin = bin_count(c);
   const long long scan_blocks = (nbin + 1 + 8191) / 8192;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -112,6 +131,9 @@ Layout layout(const pibm_config* c) {
   L.mass = take(sizeof(double) * np);
   L.Ap = take(sizeof(double) * np);
   L.buoy = take(sizeof(double) * np);
+  L.gw = take(sizeof(double) * np);
+  L.radf = take(sizeof(float) * np);
+  L.xf = take(sizeof(float) * d * np);
   L.g = take(sizeof(double) * d * np);
   L.Fc = take(sizeof(double) * d * np);
   L.key = take(sizeof(unsigned) * np);
@@ -134,6 +156,7 @@ int enqueue_step(pibm_t* h, cudaStream_t st) {
   State& s = h->s;
   int nk = 0;
   CK(launch_bin(s, st, &nk));
+  CK(launch_contacts(s, st, &nk));
   CK(launch_couple(s, st, &nk));
   CK(launch_collide_stream(s, st));
   nk += 1;
@@ -294,6 +317,9 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
   P.mass = (double*)(base + L.mass);
   P.Ap = (double*)(base + L.Ap);
   P.buoy = (double*)(base + L.buoy);
+  P.gw = (double*)(base + L.gw);
+  P.radf = (float*)(base + L.radf);
+  P.xf = (float*)(base + L.xf);
   P.g = (double*)(base + L.g);
   P.Fc = (double*)(base + L.Fc);
   P.key = (unsigned*)(base + L.key);
@@ -301,7 +327,8 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
   P.perm = (unsigned*)(base + L.perm);
   P.bin_cnt = (unsigned*)(base + L.bin);
   P.block_sums = (unsigned*)(base + L.bsum);
-  P.nbin = s.geo.ncell;
+  P.bm = bin_map(cfg);
+  P.nbin = bin_count(cfg);
   P.scan_blocks = (int)((P.nbin + 1 + 8191) / 8192);
   s.cur = 0;
 
@@ -378,7 +405,7 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
       return fail(PIBM_ECUDA);
   }
   if (cudaStreamSynchronize(st) != cudaSuccess) return fail(PIBM_ECUDA);
-  h->kernels_per_step = np > 0 ? (s.deterministic ? 9 : 8) : 1;
+  h->kernels_per_step = np > 0 ? (s.deterministic ? 10 : 9) : 1;
   *out = h;
   return PIBM_OK;
 }
@@ -512,11 +539,12 @@ int pibm_kernels_per_step(pibm_t* h) { return h ? h->kernels_per_step : 0; }
 int pibm_profile_steps(pibm_t* h, int64_t nsteps, double* phase_ms) {
   if (!h || nsteps < 0 || !phase_ms) return PIBM_EINVAL;
   DeviceGuard guard(h->device);
-  for (int k = 0; k < 4; ++k) phase_ms[k] = 0.0;
+  constexpr int NP = 4;  // bin, contacts, coupling, collide-stream
+  for (int k = 0; k <= NP; ++k) phase_ms[k] = 0.0;
   if (nsteps == 0) return health(h);
   State& s = h->s;
   cudaStream_t st = h->stream;
-  std::vector<cudaEvent_t> ev((size_t)3 * nsteps + 1, nullptr);
+  std::vector<cudaEvent_t> ev((size_t)NP * nsteps + 1, nullptr);
   int rc = PIBM_OK;
   for (auto& e : ev)
     if (cudaEventCreate(&e) != cudaSuccess) rc = PIBM_ECUDA;
@@ -524,13 +552,13 @@ int pibm_profile_steps(pibm_t* h, int64_t nsteps, double* phase_ms) {
     int nk = 0;
     if (cudaEventRecord(ev[0], st) != cudaSuccess) rc = PIBM_ECUDA;
     for (int64_t i = 0; i < nsteps && rc == PIBM_OK; ++i) {
-      nk = 0;
-      if (launch_bin(s, st, &nk) != cudaSuccess ||
-          cudaEventRecord(ev[3 * i + 1], st) != cudaSuccess ||
-          launch_couple(s, st, &nk) != cudaSuccess ||
-          cudaEventRecord(ev[3 * i + 2], st) != cudaSuccess ||
+      cudaEvent_t* e = &ev[NP * i + 1];
+      if (launch_bin(s, st, &nk) != cudaSuccess || cudaEventRecord(e[0], st) != cudaSuccess ||
+          launch_contacts(s, st, &nk) != cudaSuccess ||
+          cudaEventRecord(e[1], st) != cudaSuccess ||
+          launch_couple(s, st, &nk) != cudaSuccess || cudaEventRecord(e[2], st) != cudaSuccess ||
           launch_collide_stream(s, st) != cudaSuccess ||
-          cudaEventRecord(ev[3 * i + 3], st) != cudaSuccess) {
+          cudaEventRecord(e[3], st) != cudaSuccess) {
         rc = PIBM_ECUDA;
         break;
       }
@@ -538,19 +566,17 @@ int pibm_profile_steps(pibm_t* h, int64_t nsteps, double* phase_ms) {
     }
     if (rc == PIBM_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = PIBM_ECUDA;
     for (int64_t i = 0; i < nsteps && rc == PIBM_OK; ++i) {
-      float t[3];
-      for (int k = 0; k < 3; ++k) {
-        if (cudaEventElapsedTime(&t[k], ev[3 * i + k], ev[3 * i + k + 1]) != cudaSuccess) {
+      for (int k = 0; k < NP; ++k) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, ev[NP * i + k], ev[NP * i + k + 1]) != cudaSuccess)
           rc = PIBM_ECUDA;
-          t[k] = 0.f;
-        }
-        phase_ms[k] += t[k];
+        phase_ms[k] += t;
       }
     }
     float tot = 0.f;
-    if (rc == PIBM_OK && cudaEventElapsedTime(&tot, ev[0], ev[3 * nsteps]) != cudaSuccess)
+    if (rc == PIBM_OK && cudaEventElapsedTime(&tot, ev[0], ev[NP * nsteps]) != cudaSuccess)
       rc = PIBM_ECUDA;
-    phase_ms[3] = tot;
+    phase_ms[NP] = tot;
   }
   for (auto& e : ev)
     if (e) cudaEventDestroy(e);

@@ -57,7 +57,8 @@ template <int Q, class St, typename FT>
 __global__ void __launch_bounds__(256) k_collide_stream(const typename St::T* __restrict__ fin,
                                                         typename St::T* __restrict__ fout,
                                                         FT* __restrict__ F, Geometry g,
-                                                        double omega_d, double cF_d,
+                                                        typename St::R om,
+                                                        typename St::R cF,
                                                         unsigned* __restrict__ err) {
   using L = Lattice<Q>;
   using T = typename St::T;
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(256) k_collide_stream(const typename St::T* __
     uu += u[k] * u[k];
     uF += u[k] * Fv[k];
   }
-  const R om = (R)omega_d, cF = (R)cF_d, om1 = R(1) - om;
+  const R om1 = R(1) - om;
   // Equilibrium minus the stored shift, Eq. (3):
   //   feq_a - S w_a = w_a sum + rho w_a (3 eu + 4.5 eu^2 - 1.5 uu)
   // Guo term, Eq. (8): cF w_a (3 (e_a - u).F + 9 (e_a.u)(e_a.F)).
@@ -301,8 +302,10 @@ cudaError_t collide_stream_t(const State& s, cudaStream_t st) {
   dim3 blk = cell_block(g);
   dim3 grd((g.n[0] + blk.x - 1) / blk.x, (g.n[1] + blk.y - 1) / blk.y, g.n[2]);
   using T = typename St::T;
+  using R = typename St::R;
   k_collide_stream<Q, St, FT><<<grd, blk, 0, st>>>((const T*)s.f[s.cur], (T*)s.f[1 - s.cur],
-                                                   (FT*)s.F, g, s.phy.omega, s.phy.cF, s.err);
+                                                   (FT*)s.F, g, (R)s.phy.omega, (R)s.phy.cF,
+                                                   s.err);
   return cudaGetLastError();
 }
 

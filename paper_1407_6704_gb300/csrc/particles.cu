@@ -31,17 +31,32 @@ __device__ __forceinline__ int bin_coord(double X, int n) {
 }
 
 template <int D>
-__global__ void k_bin_key(const double* __restrict__ X, long long np, Geometry g,
+__device__ __forceinline__ unsigned bin_index(const BinMap& b, int x, int y, int z) {
+  using TD = TileDims<D>;
+  const int tx = x / TD::TX, ty = y / TD::TY, tz = z / TD::TZ;
+  const int lx = x - tx * TD::TX, ly = y - ty * TD::TY, lz = z - tz * TD::TZ;
+  return (unsigned)(tx + b.nt[0] * (ty + b.nt[1] * tz)) * (unsigned)TD::TC +
+         (unsigned)(lx + TD::TX * (ly + TD::TY * lz));
+}
+
+// Bins are lattice cells, numbered tile-major: the cells of one tile form a
+// contiguous bin range, so after sorting its particles form one contiguous range.
+template <int D>
+__global__ void k_bin_key(const double* __restrict__ X, long long np, Geometry g, BinMap bm,
                           unsigned* __restrict__ key, unsigned* __restrict__ rank,
-                          unsigned* __restrict__ cnt) {
+                          unsigned* __restrict__ cnt, float* __restrict__ xf) {
   long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= np) return;
-  int b0 = bin_coord(X[p], g.n[0]);
-  int b1 = bin_coord(X[np + p], g.n[1]);
-  int b2 = D == 3 ? bin_coord(X[2 * np + p], g.n[2]) : 0;
-  unsigned k = (unsigned)(b0 + (long long)g.n[0] * (b1 + (long long)g.n[1] * b2));
-  key[p] = k;
-  rank[p] = atomicAdd(&cnt[k], 1u);
+  int b[3] = {0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const double x = X[k * np + p];
+    b[k] = bin_coord(x, g.n[k]);
+    xf[k * np + p] = (float)x;
+  }
+  unsigned kk = bin_index<D>(bm, b[0], b[1], b[2]);
+  key[p] = kk;
+  rank[p] = atomicAdd(&cnt[kk], 1u);
 }
 
 // Block-wide exclusive scan of SCAN_CHUNK unsigned values; returns the total.
@@ -82,14 +97,28 @@ __device__ unsigned block_scan(unsigned (&v)[SCAN_PER_THREAD], unsigned* sm) {
   return total;
 }
 
+// Eight consecutive counts per thread; full groups move as two 16-byte vectors
+// (the array is 256-byte aligned and every group starts at a multiple of 8).
+__device__ __forceinline__ void load8(const unsigned* __restrict__ in, long long base, long long n,
+                                      unsigned (&v)[SCAN_PER_THREAD]) {
+  if (base + SCAN_PER_THREAD <= n) {
+    const uint4 a = *reinterpret_cast<const uint4*>(in + base);
+    const uint4 b = *reinterpret_cast<const uint4*>(in + base + 4);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < SCAN_PER_THREAD; ++i) v[i] = (base + i < n) ? in[base + i] : 0u;
+  }
+}
+
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const unsigned* __restrict__ in,
                                                               long long n,
                                                               unsigned* __restrict__ sums) {
   __shared__ unsigned sm[33];
   long long base = blockIdx.x * (long long)SCAN_CHUNK + threadIdx.x * SCAN_PER_THREAD;
   unsigned v[SCAN_PER_THREAD];
-#pragma unroll
-  for (int i = 0; i < SCAN_PER_THREAD; ++i) v[i] = (base + i < n) ? in[base + i] : 0u;
+  load8(in, base, n, v);
   unsigned total = block_scan(v, sm);
   if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
@@ -112,13 +141,17 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(unsigned* __restrict
   __shared__ unsigned sm[33];
   long long base = blockIdx.x * (long long)SCAN_CHUNK + threadIdx.x * SCAN_PER_THREAD;
   unsigned v[SCAN_PER_THREAD];
-#pragma unroll
-  for (int i = 0; i < SCAN_PER_THREAD; ++i) v[i] = (base + i < n) ? data[base + i] : 0u;
+  load8(data, base, n, v);
   block_scan(v, sm);
-  unsigned off = sums[blockIdx.x];
+  const unsigned off = sums[blockIdx.x];
+  if (base + SCAN_PER_THREAD <= n) {
+    *reinterpret_cast<uint4*>(data + base) = make_uint4(v[0] + off, v[1] + off, v[2] + off, v[3] + off);
+    *reinterpret_cast<uint4*>(data + base + 4) = make_uint4(v[4] + off, v[5] + off, v[6] + off, v[7] + off);
+  } else {
 #pragma unroll
-  for (int i = 0; i < SCAN_PER_THREAD; ++i)
-    if (base + i < n) data[base + i] = v[i] + off;
+    for (int i = 0; i < SCAN_PER_THREAD; ++i)
+      if (base + i < n) data[base + i] = v[i] + off;
+  }
 }
 
 // Place each particle at its slot, then order every bin by particle id so that
@@ -152,47 +185,51 @@ __global__ void k_bin_sort(const unsigned* __restrict__ key, const unsigned* __r
 // ---------------------------------------------------------------------------
 // Delta weights along one axis (Eqs. 10-11 and the 2-point hat)
 // ---------------------------------------------------------------------------
-template <int W>
+template <int W, typename WT>
 struct Taps {
-  int idx[W];
-  double w[W];
+  int first;    // unwrapped index of the first node
+  int idx[W];   // wrapped (periodic) or clamped (dropped wall node) index
+  WT w[W];
 };
+
+__device__ __forceinline__ void sincospi_t(double a, double* s, double* c) { sincospi(a, s, c); }
+__device__ __forceinline__ void sincospi_t(float a, float* s, float* c) { sincospif(a, s, c); }
 
 // b = floor(X - 1/2); nodes b..b+1 (W = 2) or b-1..b+2 (W = 4) at distance
 // r_t = first + t + 1/2 - X. For the cosine kernel the four values are
 // 1/4 (1 + cos th), 1/4 (1 - sin th), 1/4 (1 - cos th), 1/4 (1 + sin th) with
 // th = pi r_0 / 2 (cos shifts by a quarter period per node). On a wall axis the
 // nodes outside [0, n) are dropped (weight 0) and the kept weights renormalised.
-template <int W>
-__device__ __forceinline__ void axis_taps(double X, int n, int periodic, Taps<W>& t) {
-  int b = (int)floor(X - 0.5);
-  int first = (W == 2) ? b : b - 1;
-  double r0 = (double)first + 0.5 - X;
+template <int W, typename WT>
+__device__ __forceinline__ void axis_taps(double X, int n, int periodic, Taps<W, WT>& t) {
+  const int b = (int)floor(X - 0.5);
+  t.first = (W == 2) ? b : b - 1;
+  const WT r0 = (WT)((double)t.first + 0.5 - X);
   if constexpr (W == 2) {
-    t.w[0] = 1.0 + r0;  // 1 - |r0|, r0 in (-1, 0]
-    t.w[1] = -r0;       // 1 - |r0 + 1|
+    t.w[0] = WT(1) + r0;  // 1 - |r0|, r0 in (-1, 0]
+    t.w[1] = -r0;         // 1 - |r0 + 1|
   } else {
-    double sn, cs;
-    sincospi(0.5 * r0, &sn, &cs);
-    t.w[0] = 0.25 * (1.0 + cs);
-    t.w[1] = 0.25 * (1.0 - sn);
-    t.w[2] = 0.25 * (1.0 - cs);
-    t.w[3] = 0.25 * (1.0 + sn);
+    WT sn, cs;
+    sincospi_t(WT(0.5) * r0, &sn, &cs);
+    t.w[0] = WT(0.25) * (WT(1) + cs);
+    t.w[1] = WT(0.25) * (WT(1) - sn);
+    t.w[2] = WT(0.25) * (WT(1) - cs);
+    t.w[3] = WT(0.25) * (WT(1) + sn);
   }
   if (periodic) {
 #pragma unroll
     for (int i = 0; i < W; ++i) {
-      int k = (first + i) % n;  // any X (even a non-finite one) maps into [0, n)
+      int k = (t.first + i) % n;  // any X (even a non-finite one) maps into [0, n)
       t.idx[i] = k < 0 ? k + n : k;
     }
   } else {
-    double s = 0.0;
+    WT s = WT(0);
 #pragma unroll
     for (int i = 0; i < W; ++i) {
-      int k = first + i;
+      int k = t.first + i;
       bool in = (k >= 0 && k < n);
       t.idx[i] = in ? k : 0;
-      if (!in) t.w[i] = 0.0;
+      if (!in) t.w[i] = WT(0);
       s += t.w[i];
     }
 #pragma unroll
@@ -200,14 +237,26 @@ __device__ __forceinline__ void axis_taps(double X, int n, int periodic, Taps<W>
   }
 }
 
-// Post-stream moments (rho, j) at cell (x, y, z) pulled from the stored f*.
+// Wrap a region coordinate onto the lattice: periodic axes wrap, wall axes
+// report cells outside [0, n).
+__device__ __forceinline__ bool lattice_coord(int& x, int n, int periodic) {
+  if (x >= 0 && x < n) return true;
+  if (!periodic) return false;
+  x %= n;
+  if (x < 0) x += n;
+  return true;
+}
+
+// Post-stream moments at lattice cell (x, y, z), pulled from the stored f*:
+// sum of the stored values (rho - S) and the first moment j, in type R.
 template <int Q, class St>
-__device__ __forceinline__ void tap_moments(const typename St::T* __restrict__ f,
-                                            const Geometry& g, int x, int y, int z, double& rho,
-                                            double (&j)[3]) {
+__device__ __forceinline__ void pull_moments(const typename St::T* __restrict__ f,
+                                             const Geometry& g, int x, int y, int z,
+                                             typename St::R& r, typename St::R (&j)[3]) {
   using L = Lattice<Q>;
+  using R = typename St::R;
   const long long c = x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
-  double r = St::S ? 1.0 : 0.0, m0 = 0.0, m1 = 0.0, m2 = 0.0;
+  R s = R(0), m0 = R(0), m1 = R(0), m2 = R(0);
 #pragma unroll
   for (int a = 0; a < Q; ++a) {
     int s0 = x - L::e(a, 0), s1 = y - L::e(a, 1), s2 = z - L::e(a, 2);
@@ -225,13 +274,13 @@ __device__ __forceinline__ void tap_moments(const typename St::T* __restrict__ f
       else if (s2 >= g.n[2]) { if (g.periodic[2]) s2 -= g.n[2]; else bb = true; }
     }
     long long src = s0 + (long long)g.n[0] * (s1 + (long long)g.n[1] * s2);
-    double v = (double)(bb ? f[opp(a) * g.pitch + c] : f[a * g.pitch + src]);
-    r += v;
+    R v = (R)(bb ? f[opp(a) * g.pitch + c] : f[a * g.pitch + src]);
+    s += v;
     if (L::e(a, 0)) m0 += L::e(a, 0) * v;
     if (L::e(a, 1)) m1 += L::e(a, 1) * v;
     if (L::e(a, 2)) m2 += L::e(a, 2) * v;
   }
-  rho = r;
+  r = s;
   j[0] = m0;
   j[1] = m1;
   j[2] = m2;
@@ -249,6 +298,7 @@ __device__ __forceinline__ double min_image(double s, int n, int periodic) {
 struct CoupleArgs {
   Geometry g;
   Physics ph;
+  BinMap bm;
   long long np;
   const double* X;   // [d][np], step n
   const double* U;
@@ -258,6 +308,10 @@ struct CoupleArgs {
   const double* mass;
   const double* Ap;
   const double* buoy;
+  const double* gw;     // wall damping coefficient per particle
+  const float* radf;    // radius (FP32)
+  const float* xf;      // [d][np] FP32 positions of step n
+  float xf_margin;      // bound on the FP32 rounding error of a distance
   double* gout;      // [d][np]
   double* Fcout;     // [d][np]
   const unsigned* perm;
@@ -265,201 +319,297 @@ struct CoupleArgs {
   const void* f;     // stored populations f*
   void* F;           // force field
   unsigned* err;
-  int spread;        // 1: scatter A_p g into F with atomics
+  int spread;        // 1: spread A_p g into F (through the tile's shared-memory copy)
 };
 
-__device__ __forceinline__ void atomic_add_f(double* a, double v) { atomicAdd(a, v); }
-__device__ __forceinline__ void atomic_add_f(float* a, double v) { atomicAdd(a, (float)v); }
-
-template <int Q, int W, class St, typename FT>
-__global__ void __launch_bounds__(128) k_couple(CoupleArgs A) {
-  using L = Lattice<Q>;
-  using T = typename St::T;
-  constexpr int D = L::D;
-  const long long slot = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (slot >= A.np) return;
+// Contact forces (linear spring-dashpot, normal only) on the step-n state, one
+// thread per particle in sorted order: the 3^d neighbouring cells through the
+// cell list, then the walls. gamma = 2 beta sqrt(m_eff kn) with
+// beta = -ln e / sqrt(pi^2 + ln^2 e) fixes the restitution coefficient e.
+// Candidates are first screened in FP32 with a margin larger than the FP32
+// rounding of the positions (xf_margin), so only pairs that may overlap reach
+// the FP64 overlap test; the force itself is FP64.
+template <int D>
+__global__ void __launch_bounds__(256) k_contacts(CoupleArgs A) {
+  const long long sl = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (sl >= A.np) return;
   const Geometry& g = A.g;
+  const BinMap& bm = A.bm;
   const long long np = A.np;
-  const unsigned p = A.perm[slot];
-
-  double X[3] = {0.0, 0.0, 0.0}, U[3] = {0.0, 0.0, 0.0};
+  const unsigned p = A.perm[sl];
+  const float mrg = A.xf_margin;
+  float xp[3] = {0.f, 0.f, 0.f};
+  int bc[3] = {0, 0, 0};
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    X[k] = A.X[k * np + p];
-    U[k] = A.U[k * np + p];
+    xp[k] = A.xf[k * np + p];
+    bc[k] = bin_coord(A.X[k * np + p], g.n[k]);
   }
-
-  // --- interpolation of rho, j (Eq. 4) ---
-  Taps<W> tx, ty, tz;
-  axis_taps<W>(X[0], g.n[0], g.periodic[0], tx);
-  axis_taps<W>(X[1], g.n[1], g.periodic[1], ty);
-  if (D == 3) axis_taps<W>(X[2], g.n[2], g.periodic[2], tz);
-  const T* f = (const T*)A.f;
-  double rho_l = 0.0, j_l[3] = {0.0, 0.0, 0.0};
-  constexpr int WZ = (D == 3) ? W : 1;
-#pragma unroll 1
-  for (int iz = 0; iz < WZ; ++iz) {
-    const double wz = (D == 3) ? tz.w[iz] : 1.0;
-    const int z = (D == 3) ? tz.idx[iz] : 0;
-    if (wz == 0.0) continue;
-#pragma unroll 1
-    for (int iy = 0; iy < W; ++iy) {
-      const double wyz = ty.w[iy] * wz;
-      if (wyz == 0.0) continue;
-#pragma unroll 1
-      for (int ix = 0; ix < W; ++ix) {
-        const double wt = tx.w[ix] * wyz;
-        if (wt == 0.0) continue;
-        double r, jj[3];
-        tap_moments<Q, St>(f, g, tx.idx[ix], ty.idx[iy], z, r, jj);
-        rho_l += wt * r;
-#pragma unroll
-        for (int k = 0; k < D; ++k) j_l[k] += wt * jj[k];
-      }
-    }
-  }
-
-  // --- contacts over the 3^d neighbouring bins, then the walls ---
-  const double ri = A.rad[p], mi = A.mass[p];
+  const float rpf = A.radf[p];
   double Fc[3] = {0.0, 0.0, 0.0};
-  int bc[3] = {bin_coord(X[0], g.n[0]), bin_coord(X[1], g.n[1]),
-               D == 3 ? bin_coord(X[2], g.n[2]) : 0};
-  const double kn = A.ph.kn, beta = A.ph.beta;
 #pragma unroll 1
   for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz) {
     int cz = bc[2] + oz;
-    if (D == 3) {
-      if (cz < 0 || cz >= g.n[2]) {
-        if (!g.periodic[2]) continue;
-        cz = cz < 0 ? cz + g.n[2] : cz - g.n[2];
-      }
-    }
+    if (D == 3 && !lattice_coord(cz, g.n[2], g.periodic[2])) continue;
 #pragma unroll 1
     for (int oy = -1; oy <= 1; ++oy) {
       int cy = bc[1] + oy;
-      if (cy < 0 || cy >= g.n[1]) {
-        if (!g.periodic[1]) continue;
-        cy = cy < 0 ? cy + g.n[1] : cy - g.n[1];
-      }
+      if (!lattice_coord(cy, g.n[1], g.periodic[1])) continue;
 #pragma unroll 1
       for (int ox = -1; ox <= 1; ++ox) {
         int cx = bc[0] + ox;
-        if (cx < 0 || cx >= g.n[0]) {
-          if (!g.periodic[0]) continue;
-          cx = cx < 0 ? cx + g.n[0] : cx - g.n[0];
-        }
-        const long long b = cx + (long long)g.n[0] * (cy + (long long)g.n[1] * cz);
+        if (!lattice_coord(cx, g.n[0], g.periodic[0])) continue;
+        const unsigned b = bin_index<D>(bm, cx, cy, cz);
         const unsigned lo = A.start[b], hi = A.start[b + 1];
-        for (unsigned sl = lo; sl < hi; ++sl) {
-          const unsigned q = A.perm[sl];
+        for (unsigned s2 = lo; s2 < hi; ++s2) {
+          const unsigned q = A.perm[s2];
           if (q == p) continue;
-          double s[3], d2 = 0.0;
+          float d2f = 0.f;
 #pragma unroll
           for (int k = 0; k < D; ++k) {
+            float s = xp[k] - A.xf[k * np + q];
+            if (g.periodic[k]) {
+              const float N = (float)g.n[k];
+              if (s > 0.5f * N) s -= N;
+              if (s < -0.5f * N) s += N;
+            }
+            d2f += s * s;
+          }
+          const float reach = rpf + A.radf[q] + mrg;
+          if (d2f > reach * reach) continue;
+          // FP64 overlap test and force
+          double X[3], s[3], d2 = 0.0;
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            X[k] = A.X[k * np + p];
             s[k] = min_image(X[k] - A.X[k * np + q], g.n[k], g.periodic[k]);
             d2 += s[k] * s[k];
           }
           const double dist = sqrt(d2);
-          const double delta = ri + A.rad[q] - dist;
+          const double delta = A.rad[p] + A.rad[q] - dist;
           if (!(delta > 0.0) || !(dist > 0.0)) continue;
-          const double mq = A.mass[q];
+          const double mi = A.mass[p], mq = A.mass[q];
           const double meff = mi * mq / (mi + mq);
-          const double gam = 2.0 * beta * sqrt(meff * kn);
+          const double gam = 2.0 * A.ph.beta * sqrt(meff * A.ph.kn);
           const double inv = 1.0 / dist;
           double vn = 0.0;
 #pragma unroll
-          for (int k = 0; k < D; ++k) vn += (U[k] - A.U[k * np + q]) * (s[k] * inv);
-          const double mag = kn * delta - gam * vn;
+          for (int k = 0; k < D; ++k) vn += (A.U[k * np + p] - A.U[k * np + q]) * (s[k] * inv);
+          const double mag = A.ph.kn * delta - gam * vn;
 #pragma unroll
           for (int k = 0; k < D; ++k) Fc[k] += mag * (s[k] * inv);
         }
       }
     }
   }
-  {
-    const double gw = 2.0 * beta * sqrt(mi * kn);
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      if (g.periodic[k]) continue;
-      double delta = ri - X[k];
-      if (delta > 0.0) Fc[k] += kn * delta - gw * U[k];
-      delta = ri - ((double)g.n[k] - X[k]);
-      if (delta > 0.0) Fc[k] -= kn * delta + gw * U[k];
-    }
-  }
-
-  // --- particle update (Eq. 13) and force density (Eqs. 6-7) ---
-  const double Ap = A.Ap[p], bu = A.buoy[p];
-  double Un[3], Ub[3], gg[3];
-  if (A.ph.implicit_drag) {
-    const double inv = 1.0 / (mi + 2.0 * Ap * rho_l);
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      Un[k] = (mi * U[k] + 2.0 * Ap * j_l[k] + bu * A.ph.gravity[k] + Fc[k]) * inv;
-      Ub[k] = Un[k];
-    }
-  } else {
-    const double invm = 1.0 / mi;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      Un[k] = U[k] + (bu * A.ph.gravity[k] + Fc[k] - Ap * 2.0 * (rho_l * U[k] - j_l[k])) * invm;
-      Ub[k] = U[k];
-    }
-  }
-  bool bad = false, esc = false;
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    gg[k] = 2.0 * (rho_l * Ub[k] - j_l[k]);
-    double xn = X[k] + Un[k];
-    if (g.periodic[k]) {
-      const double N = (double)g.n[k];
-      if (xn < 0.0) xn += N;
-      else if (xn >= N) xn -= N;
-      if (!(xn >= 0.0 && xn < N)) xn = xn - N * floor(xn / N);  // |U| > N: not physical
-      if (!(xn >= 0.0 && xn < N)) xn = 0.0;
-    } else if (xn < 0.0 || xn > (double)g.n[k]) {
-      esc = true;
+    if (g.periodic[k]) continue;
+    const float nk = (float)g.n[k];
+    if (xp[k] < rpf + mrg) {  // near the wall at 0 (normal +e_k)
+      const double delta = A.rad[p] - A.X[k * np + p];
+      if (delta > 0.0) Fc[k] += A.ph.kn * delta - A.gw[p] * A.U[k * np + p];
     }
-    bad |= !isfinite(xn) || !isfinite(Un[k]);
-    A.Xn[k * np + p] = xn;
-    A.Un[k * np + p] = Un[k];
-    A.gout[k * np + p] = gg[k];
-    A.Fcout[k * np + p] = Fc[k];
+    if (xp[k] > nk - rpf - mrg) {  // near the wall at n (normal -e_k)
+      const double delta = A.rad[p] - ((double)g.n[k] - A.X[k * np + p]);
+      if (delta > 0.0) Fc[k] -= A.ph.kn * delta + A.gw[p] * A.U[k * np + p];
+    }
   }
-  if (bad) atomicOr(A.err, ERR_PARTICLE_NONFINITE);
-  if (esc) atomicOr(A.err, ERR_ESCAPED);
+#pragma unroll
+  for (int k = 0; k < D; ++k) A.Fcout[k * np + p] = Fc[k];
+}
 
-  // --- spreading (Eq. 9): F += A_p g w at the interpolation taps ---
-  if (A.spread) {
-    FT* F = (FT*)A.F;
-    const long long P = g.pitch;
+template <int D, int W>
+struct TileShape {
+  static constexpr int H = W / 2;  // halo: the stencil of a particle in a tile cell
+  static constexpr int TX = TileDims<D>::TX, TY = TileDims<D>::TY, TZ = TileDims<D>::TZ;
+  static constexpr int RX = TX + 2 * H, RY = TY + 2 * H, RZ = D == 2 ? 1 : TZ + 2 * H;
+  static constexpr int RC = RX * RY * RZ;
+};
+
+// One CTA per tile of lattice cells (tile-major bins make its particles one
+// contiguous range of the sorted list):
+//  1. the post-stream moments of every cell of the tile plus a halo of W/2
+//     cells (every node a particle of the tile can touch) go to shared memory;
+//  2. each particle of the tile interpolates from them, sums its contacts,
+//     advances, forms g and spreads A_p g w into a shared-memory copy of F over
+//     the same region;
+//  3. the region's non-zero F entries are added to the global field.
+// Tiles without particles return at once.
+template <int Q, int W, class St, typename FT>
+__global__ void __launch_bounds__(128) k_couple(CoupleArgs A) {
+  using L = Lattice<Q>;
+  using T = typename St::T;
+  using R = typename St::R;
+  constexpr int D = L::D;
+  using TS = TileShape<D, W>;
+  constexpr int RX = TS::RX, RY = TS::RY, RC = TS::RC;
+  const Geometry& g = A.g;
+  const BinMap& bm = A.bm;
+  const unsigned tile = blockIdx.x;
+  const unsigned p0 = A.start[tile * (unsigned)bm.tc];
+  const unsigned p1 = A.start[(tile + 1) * (unsigned)bm.tc];
+  if (p0 == p1) return;
+  const int t0 = tile % bm.nt[0], t1 = (tile / bm.nt[0]) % bm.nt[1];
+  const int t2 = tile / (bm.nt[0] * bm.nt[1]);
+  const int o0 = t0 * TS::TX - TS::H, o1 = t1 * TS::TY - TS::H;
+  const int o2 = D == 3 ? t2 * TS::TZ - TS::H : 0;
+
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R* mom = (R*)smraw;                                  // [D + 1][RC]
+  FT* Fs = (FT*)(smraw + sizeof(R) * (D + 1) * RC);   // [D][RC]
+  const T* f = (const T*)A.f;
+
+  for (int i = threadIdx.x; i < RC; i += blockDim.x) {
+    int x = o0 + i % RX, y = o1 + (i / RX) % RY, z = o2 + i / (RX * RY);
+    R r = R(0), j[3] = {R(0), R(0), R(0)};
+    if (lattice_coord(x, g.n[0], g.periodic[0]) && lattice_coord(y, g.n[1], g.periodic[1]) &&
+        lattice_coord(z, g.n[2], g.periodic[2]))
+      pull_moments<Q, St>(f, g, x, y, z, r, j);
+    mom[i] = r;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      mom[(k + 1) * RC + i] = j[k];
+      Fs[k * RC + i] = FT(0);
+    }
+  }
+  __syncthreads();
+
+  const long long np = A.np;
+  for (unsigned sl = p0 + threadIdx.x; sl < p1; sl += blockDim.x) {
+    const unsigned p = A.perm[sl];
+    double X[3] = {0.0, 0.0, 0.0}, U[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      X[k] = A.X[k * np + p];
+      U[k] = A.U[k * np + p];
+    }
+    // --- interpolation of rho, j (Eq. 4) from the staged moments ---
+    Taps<W, R> tx, ty, tz;
+    axis_taps<W, R>(X[0], g.n[0], g.periodic[0], tx);
+    axis_taps<W, R>(X[1], g.n[1], g.periodic[1], ty);
+    if constexpr (D == 3) axis_taps<W, R>(X[2], g.n[2], g.periodic[2], tz);
+    const int lx0 = tx.first - o0, ly0 = ty.first - o1;
+    int lz0 = 0;
+    if constexpr (D == 3) lz0 = tz.first - o2;
+    R rs = R(0), js[3] = {R(0), R(0), R(0)};
+    constexpr int WZ = D == 3 ? W : 1;
 #pragma unroll 1
     for (int iz = 0; iz < WZ; ++iz) {
-      const double wz = (D == 3) ? tz.w[iz] : 1.0;
-      const int z = (D == 3) ? tz.idx[iz] : 0;
-      if (wz == 0.0) continue;
-#pragma unroll 1
-      for (int iy = 0; iy < W; ++iy) {
-        const double wyz = ty.w[iy] * wz;
-        if (wyz == 0.0) continue;
-#pragma unroll 1
-        for (int ix = 0; ix < W; ++ix) {
-          const double wt = tx.w[ix] * wyz;
-          if (wt == 0.0) continue;
-          const long long c = tx.idx[ix] + (long long)g.n[0] * (ty.idx[iy] + (long long)g.n[1] * z);
+      R wz = R(1);
+      if constexpr (D == 3) wz = tz.w[iz];
 #pragma unroll
-          for (int k = 0; k < D; ++k) atomic_add_f(&F[k * P + c], Ap * gg[k] * wt);
+      for (int iy = 0; iy < W; ++iy) {
+        const R wyz = ty.w[iy] * wz;
+        const int row = ((lz0 + iz) * RY + (ly0 + iy)) * RX + lx0;
+#pragma unroll
+        for (int ix = 0; ix < W; ++ix) {
+          const R wt = tx.w[ix] * wyz;
+          rs += wt * mom[row + ix];
+#pragma unroll
+          for (int k = 0; k < D; ++k) js[k] += wt * mom[(k + 1) * RC + row + ix];
+        }
+      }
+    }
+    const double rho_l = (double)St::S + (double)rs;
+    double j_l[3] = {(double)js[0], (double)js[1], (double)js[2]};
+
+    // --- contact force of this step (k_contacts) ---
+    const double mi = A.mass[p];
+    double Fc[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < D; ++k) Fc[k] = A.Fcout[k * np + p];
+
+    // --- particle update (Eq. 13) and force density (Eqs. 6-7) ---
+    const double Ap = A.Ap[p], bu = A.buoy[p];
+    double Un[3], Ub[3], gg[3];
+    if (A.ph.implicit_drag) {
+      const double inv = 1.0 / (mi + 2.0 * Ap * rho_l);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        Un[k] = (mi * U[k] + 2.0 * Ap * j_l[k] + bu * A.ph.gravity[k] + Fc[k]) * inv;
+        Ub[k] = Un[k];
+      }
+    } else {
+      const double invm = 1.0 / mi;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        Un[k] = U[k] + (bu * A.ph.gravity[k] + Fc[k] - Ap * 2.0 * (rho_l * U[k] - j_l[k])) * invm;
+        Ub[k] = U[k];
+      }
+    }
+    bool bad = false, esc = false;
+    FT amp[3];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      gg[k] = 2.0 * (rho_l * Ub[k] - j_l[k]);
+      amp[k] = (FT)(Ap * gg[k]);
+      double xn = X[k] + Un[k];
+      if (g.periodic[k]) {
+        const double N = (double)g.n[k];
+        if (xn < 0.0) xn += N;
+        else if (xn >= N) xn -= N;
+        if (!(xn >= 0.0 && xn < N)) xn = xn - N * floor(xn / N);  // |U| > N: not physical
+        if (!(xn >= 0.0 && xn < N)) xn = 0.0;
+      } else if (xn < 0.0 || xn > (double)g.n[k]) {
+        esc = true;
+      }
+      bad |= !isfinite(xn) || !isfinite(Un[k]);
+      A.Xn[k * np + p] = xn;
+      A.Un[k * np + p] = Un[k];
+      A.gout[k * np + p] = gg[k];
+    }
+    if (bad) atomicOr(A.err, ERR_PARTICLE_NONFINITE);
+    if (esc) atomicOr(A.err, ERR_ESCAPED);
+
+    // --- spreading (Eq. 9) into the shared-memory copy of F ---
+    if (A.spread) {
+#pragma unroll 1
+      for (int iz = 0; iz < WZ; ++iz) {
+        FT wz = FT(1);
+        if constexpr (D == 3) wz = (FT)tz.w[iz];
+#pragma unroll
+        for (int iy = 0; iy < W; ++iy) {
+          const FT wyz = (FT)ty.w[iy] * wz;
+          const int row = ((lz0 + iz) * RY + (ly0 + iy)) * RX + lx0;
+#pragma unroll
+          for (int ix = 0; ix < W; ++ix) {
+            const FT wt = (FT)tx.w[ix] * wyz;
+            if (wt == FT(0)) continue;
+#pragma unroll
+            for (int k = 0; k < D; ++k) atomicAdd(&Fs[k * RC + row + ix], amp[k] * wt);
+          }
         }
       }
     }
   }
+  if (!A.spread) return;
+  __syncthreads();
+  FT* F = (FT*)A.F;
+  for (int i = threadIdx.x; i < RC; i += blockDim.x) {
+    int x = o0 + i % RX, y = o1 + (i / RX) % RY, z = o2 + i / (RX * RY);
+    if (!(lattice_coord(x, g.n[0], g.periodic[0]) && lattice_coord(y, g.n[1], g.periodic[1]) &&
+          lattice_coord(z, g.n[2], g.periodic[2])))
+      continue;
+    FT v[3];
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      v[k] = Fs[k * RC + i];
+      any |= (v[k] != FT(0));
+    }
+    if (!any) continue;
+    const long long c = x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
+#pragma unroll
+    for (int k = 0; k < D; ++k) atomicAdd(&F[k * g.pitch + c], v[k]);
+  }
 }
 
-// Deterministic spreading: every cell gathers, in a fixed order (bins by
-// ascending z, y, x offset; particles by id inside a bin), the A_p g w of every
-// particle whose stencil covers it. Writes every cell of F.
+// Deterministic spreading: every cell gathers, in a fixed order (neighbour cells
+// by ascending z, y, x offset; particles by id inside a cell), the A_p g w of
+// every particle whose stencil covers it. Writes every cell of F.
 template <int D, int W, typename FT>
-__global__ void __launch_bounds__(256) k_spread_gather(Geometry g, long long np,
+__global__ void __launch_bounds__(256) k_spread_gather(Geometry g, BinMap bm, long long np,
                                                        const double* __restrict__ X,
                                                        const double* __restrict__ Ap,
                                                        const double* __restrict__ gin,
@@ -471,55 +621,46 @@ __global__ void __launch_bounds__(256) k_spread_gather(Geometry g, long long np,
   const int z = blockIdx.z;
   if (x >= g.n[0] || y >= g.n[1]) return;
   constexpr int R = (W == 2) ? 1 : 2;
-  double acc[3] = {0.0, 0.0, 0.0};
+  FT acc[3] = {FT(0), FT(0), FT(0)};
   const int cell[3] = {x, y, z};
 #pragma unroll 1
   for (int oz = (D == 3 ? -R : 0); oz <= (D == 3 ? R : 0); ++oz) {
     int cz = z + oz;
-    if (D == 3 && (cz < 0 || cz >= g.n[2])) {
-      if (!g.periodic[2]) continue;
-      cz = ((cz % g.n[2]) + g.n[2]) % g.n[2];
-    }
+    if (D == 3 && !lattice_coord(cz, g.n[2], g.periodic[2])) continue;
 #pragma unroll 1
     for (int oy = -R; oy <= R; ++oy) {
       int cy = y + oy;
-      if (cy < 0 || cy >= g.n[1]) {
-        if (!g.periodic[1]) continue;
-        cy = ((cy % g.n[1]) + g.n[1]) % g.n[1];
-      }
+      if (!lattice_coord(cy, g.n[1], g.periodic[1])) continue;
 #pragma unroll 1
       for (int ox = -R; ox <= R; ++ox) {
         int cx = x + ox;
-        if (cx < 0 || cx >= g.n[0]) {
-          if (!g.periodic[0]) continue;
-          cx = ((cx % g.n[0]) + g.n[0]) % g.n[0];
-        }
-        const long long b = cx + (long long)g.n[0] * (cy + (long long)g.n[1] * cz);
+        if (!lattice_coord(cx, g.n[0], g.periodic[0])) continue;
+        const unsigned b = bin_index<D>(bm, cx, cy, cz);
         const unsigned lo = start[b], hi = start[b + 1];
         for (unsigned sl = lo; sl < hi; ++sl) {
           const unsigned p = perm[sl];
-          double wt = 1.0;
+          FT wt = FT(1);
 #pragma unroll
           for (int k = 0; k < D; ++k) {
-            Taps<W> t;
-            axis_taps<W>(X[k * np + p], g.n[k], g.periodic[k], t);
-            double wk = 0.0;
+            Taps<W, FT> t;
+            axis_taps<W, FT>(X[k * np + p], g.n[k], g.periodic[k], t);
+            FT wk = FT(0);
 #pragma unroll
             for (int i = 0; i < W; ++i)
               if (t.idx[i] == cell[k]) wk += t.w[i];
             wt *= wk;
           }
-          if (wt == 0.0) continue;
+          if (wt == FT(0)) continue;
           const double a = Ap[p];
 #pragma unroll
-          for (int k = 0; k < D; ++k) acc[k] += a * gin[k * np + p] * wt;
+          for (int k = 0; k < D; ++k) acc[k] += (FT)(a * gin[k * np + p]) * wt;
         }
       }
     }
   }
   const long long c = x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
 #pragma unroll
-  for (int k = 0; k < D; ++k) F[k * g.pitch + c] = (FT)acc[k];
+  for (int k = 0; k < D; ++k) F[k * g.pitch + c] = acc[k];
 }
 
 __global__ void k_forces(long long np, int d, const double* __restrict__ Ap,
@@ -579,18 +720,21 @@ __global__ void k_particle_momentum_final(int d, const double* __restrict__ part
 // depth in 2D, rho_p pi d^3/6 in 3D, rho_f = 1), cross-section A_p = pi d^2/4
 // (section 2.2) and the buoyancy-reduced weight factor m (1 - rho_f/rho_p) of
 // Eq. (13).
-__global__ void k_particle_init(long long np, int d, double* __restrict__ rad,
-                                double* __restrict__ mass, double* __restrict__ Ap,
-                                double* __restrict__ buoy) {
+__global__ void k_particle_init(long long np, int d, double kn, double beta,
+                                double* __restrict__ rad, double* __restrict__ mass,
+                                double* __restrict__ Ap, double* __restrict__ buoy,
+                                double* __restrict__ gw, float* __restrict__ radf) {
   long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= np) return;
   const double dia = rad[p], rr = buoy[p];
   const double pi = 3.14159265358979323846;
   const double m = d == 2 ? rr * pi * dia * dia / 4.0 : rr * pi * dia * dia * dia / 6.0;
   rad[p] = 0.5 * dia;
+  radf[p] = (float)(0.5 * dia);
   mass[p] = m;
   Ap[p] = pi * dia * dia / 4.0;
   buoy[p] = m * (1.0 - 1.0 / rr);
+  gw[p] = 2.0 * beta * sqrt(m * kn);
 }
 
 unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -604,9 +748,11 @@ cudaError_t launch_bin(const State& s, cudaStream_t st, int* nk) {
   if (e != cudaSuccess) return e;
   const double* X = P.X[s.cur];
   if (s.geo.d == 2)
-    k_bin_key<2><<<blocks_for(P.np, 256), 256, 0, st>>>(X, P.np, s.geo, P.key, P.rank, P.bin_cnt);
+    k_bin_key<2><<<blocks_for(P.np, 256), 256, 0, st>>>(X, P.np, s.geo, P.bm, P.key, P.rank,
+                                                        P.bin_cnt, P.xf);
   else
-    k_bin_key<3><<<blocks_for(P.np, 256), 256, 0, st>>>(X, P.np, s.geo, P.key, P.rank, P.bin_cnt);
+    k_bin_key<3><<<blocks_for(P.np, 256), 256, 0, st>>>(X, P.np, s.geo, P.bm, P.key, P.rank,
+                                                        P.bin_cnt, P.xf);
   const long long n = P.nbin + 1;
   k_scan_reduce<<<P.scan_blocks, SCAN_THREADS, 0, st>>>(P.bin_cnt, n, P.block_sums);
   k_scan_top<<<1, SCAN_THREADS, 0, st>>>(P.block_sums, P.scan_blocks);
@@ -618,12 +764,12 @@ cudaError_t launch_bin(const State& s, cudaStream_t st, int* nk) {
 }
 
 namespace {
-template <int Q, int W, class St, typename FT>
-cudaError_t couple_t(const State& s, cudaStream_t st, int* nk) {
+CoupleArgs couple_args(const State& s) {
   const Particles& P = s.p;
   CoupleArgs A;
   A.g = s.geo;
   A.ph = s.phy;
+  A.bm = P.bm;
   A.np = P.np;
   A.X = P.X[s.cur];
   A.U = P.U[s.cur];
@@ -633,6 +779,15 @@ cudaError_t couple_t(const State& s, cudaStream_t st, int* nk) {
   A.mass = P.mass;
   A.Ap = P.Ap;
   A.buoy = P.buoy;
+  A.gw = P.gw;
+  A.radf = P.radf;
+  A.xf = P.xf;
+  {
+    // positions below 2^e round to FP32 within 2^(e-24) per coordinate
+    int mx = s.geo.n[0] > s.geo.n[1] ? s.geo.n[0] : s.geo.n[1];
+    mx = mx > s.geo.n[2] ? mx : s.geo.n[2];
+    A.xf_margin = 8.0f * (float)mx * 5.9604645e-8f + 1e-6f;
+  }
   A.gout = P.g;
   A.Fcout = P.Fc;
   A.perm = P.perm;
@@ -641,15 +796,33 @@ cudaError_t couple_t(const State& s, cudaStream_t st, int* nk) {
   A.F = s.F;
   A.err = s.err;
   A.spread = s.deterministic ? 0 : 1;
-  k_couple<Q, W, St, FT><<<blocks_for(P.np, 128), 128, 0, st>>>(A);
+  return A;
+}
+
+template <int Q, int W, class St, typename FT>
+cudaError_t couple_t(const State& s, cudaStream_t st, int* nk) {
+  const Particles& P = s.p;
+  constexpr int D = Lattice<Q>::D;
+  using TS = TileShape<D, W>;
+  constexpr size_t smem = sizeof(typename St::R) * (D + 1) * TS::RC + sizeof(FT) * D * TS::RC;
+  static bool attr_set = false;  // per template instance; set before the first launch
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_couple<Q, W, St, FT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  CoupleArgs A = couple_args(s);
+  const unsigned ntiles = (unsigned)(P.nbin / P.bm.tc);
+  k_couple<Q, W, St, FT><<<ntiles, 128, smem, st>>>(A);
   if (nk) *nk += 1;
   if (s.deterministic) {
     const Geometry& g = s.geo;
     int bx = g.n[0] <= 32 ? 32 : (g.n[0] <= 64 ? 64 : 128);
     dim3 blk(bx, 256 / bx, 1);
     dim3 grd((g.n[0] + blk.x - 1) / blk.x, (g.n[1] + blk.y - 1) / blk.y, g.n[2]);
-    k_spread_gather<Lattice<Q>::D, W, FT><<<grd, blk, 0, st>>>(g, P.np, P.X[s.cur], P.Ap, P.g,
-                                                               P.perm, P.bin_cnt, (FT*)s.F);
+    k_spread_gather<D, W, FT><<<grd, blk, 0, st>>>(g, P.bm, P.np, P.X[s.cur], P.Ap, P.g, P.perm,
+                                                   P.bin_cnt, (FT*)s.F);
     if (nk) *nk += 1;
   }
   return cudaGetLastError();
@@ -660,6 +833,17 @@ cudaError_t couple_w(const State& s, cudaStream_t st, int* nk) {
   return s.phy.width == 2 ? couple_t<Q, 2, St, FT>(s, st, nk) : couple_t<Q, 4, St, FT>(s, st, nk);
 }
 }  // namespace
+
+cudaError_t launch_contacts(const State& s, cudaStream_t st, int* nk) {
+  if (s.p.np == 0) return cudaSuccess;
+  CoupleArgs A = couple_args(s);
+  if (s.geo.d == 2)
+    k_contacts<2><<<blocks_for(s.p.np, 256), 256, 0, st>>>(A);
+  else
+    k_contacts<3><<<blocks_for(s.p.np, 256), 256, 0, st>>>(A);
+  if (nk) *nk += 1;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_couple(const State& s, cudaStream_t st, int* nk) {
   if (s.p.np == 0) return cudaSuccess;
@@ -703,8 +887,9 @@ cudaError_t launch_particle_momentum(const State& s, double* out_dev, cudaStream
 
 cudaError_t launch_particle_init(const State& s, cudaStream_t st) {
   if (s.p.np == 0) return cudaSuccess;
-  k_particle_init<<<blocks_for(s.p.np, 256), 256, 0, st>>>(s.p.np, s.geo.d, s.p.rad, s.p.mass,
-                                                           s.p.Ap, s.p.buoy);
+  k_particle_init<<<blocks_for(s.p.np, 256), 256, 0, st>>>(s.p.np, s.geo.d, s.phy.kn,
+                                                           s.phy.beta, s.p.rad, s.p.mass,
+                                                           s.p.Ap, s.p.buoy, s.p.gw, s.p.radf);
   return cudaGetLastError();
 }
 

@@ -102,6 +102,22 @@ struct Physics {
   int implicit_drag;
 };
 
+// Tile of lattice cells handled by one CTA of the particle kernel.
+template <int D>
+struct TileDims {
+  static constexpr int TX = D == 2 ? 32 : 16, TY = 8, TZ = D == 2 ? 1 : 4;
+  static constexpr int TC = TX * TY * TZ;
+};
+
+// Cell-list bins are lattice cells numbered tile-major (tiles of T[0] x T[1] x
+// T[2] cells, nt tiles per axis, tc = cells per tile), so that the particles of
+// one tile occupy one contiguous range of the sorted list.
+struct BinMap {
+  int T[3];
+  int nt[3];
+  int tc;
+};
+
 struct Particles {
   long long np;
   double* X[2];   // [d][np] SoA, ping-pong
@@ -110,6 +126,9 @@ struct Particles {
   double* mass;   // rho_r * (pi d^2 / 4) in 2D, rho_r * (pi d^3 / 6) in 3D
   double* Ap;     // cross-section pi d^2 / 4
   double* buoy;   // mass * (1 - 1 / rho_r)
+  double* gw;     // wall damping coefficient 2 beta sqrt(mass kn)
+  float* radf;    // radius in FP32 (contact pre-filter)
+  float* xf;      // [d][np] positions in FP32 (contact pre-filter), written by binning
   double* g;      // [d][np] force density of the last step (Eq. 7)
   double* Fc;     // [d][np] contact force of the last step
   // cell list (bins = lattice cells)
@@ -118,7 +137,8 @@ struct Particles {
   unsigned* bin_cnt;  // [nbin + 1] counts, then exclusive prefix (bin start)
   unsigned* perm;     // [np] particle id by sorted slot
   unsigned* block_sums;  // scan scratch
-  long long nbin;
+  BinMap bm;
+  long long nbin;         // tiles * cells per tile (>= ncell)
   int scan_blocks;
 };
 
@@ -151,6 +171,7 @@ cudaError_t launch_read_moment(const State& s, int comp, double* dst, cudaStream
 // Particles: binning (counting sort into lattice-cell bins) and the coupled
 // particle kernel (interpolate, contacts, update, spread).
 cudaError_t launch_bin(const State& s, cudaStream_t st, int* nkernels);
+cudaError_t launch_contacts(const State& s, cudaStream_t st, int* nkernels);
 cudaError_t launch_couple(const State& s, cudaStream_t st, int* nkernels);
 cudaError_t launch_particle_forces(const State& s, double* f_fpi, double* f_c, cudaStream_t st);
 cudaError_t launch_interleave(const State& s, const double* soa, double* aos, cudaStream_t st);

@@ -94,10 +94,10 @@ class Pibm:
 
     def profile_steps(self, nsteps):
         """Run nsteps steps phase by phase; summed device ms per phase:
-        {'bin', 'particles', 'collide_stream', 'total'}."""
-        out = np.zeros(4)
+        {'bin', 'contacts', 'couple', 'collide_stream', 'total'}."""
+        out = np.zeros(5)
         check(self._L.pibm_profile_steps(self._h, int(nsteps), _dptr(out)), "pibm_profile_steps")
-        return dict(zip(("bin", "particles", "collide_stream", "total"), out.tolist()))
+        return dict(zip(("bin", "contacts", "couple", "collide_stream", "total"), out.tolist()))
 
     def status(self):
         return self._L.pibm_status(self._h)

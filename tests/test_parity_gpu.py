@@ -134,9 +134,12 @@ def test_parity_fp64(name, kw, steps):
 
 
 def test_dense_contacts_parity():
-    """Many overlapping contacts: particles packed at a high area fraction."""
-    c = make_case(q=9, n=(20, 16), periodic=(0, 0), tau=0.7, width=2, npart=220, seed=21,
-                  dia=(0.6, 0.9), rr=2.0, band=(0.2, 1.0), kn=5e-3, u_scale=5e-3)
+    """Many overlapping contacts: a packed cloud squeezed so that neighbours overlap
+    by up to ~20 % of a diameter, then released."""
+    c = make_case(q=9, n=(24, 20), periodic=(0, 0), tau=0.7, width=2, npart=160, seed=21,
+                  dia=(0.6, 0.9), rr=2.0, band=(0.25, 0.95), kn=5e-3, u_scale=2e-3)
+    centre = np.array([12.0, 12.0])
+    c["X"] = centre + 0.85 * (c["X"] - centre)
     got, ref = run_both(c, 60)
     assert np.count_nonzero(np.abs(ref.Fc).sum(1)) > 20
     assert_parity(got, ref, c["X"])
