@@ -56,6 +56,7 @@ extern "C" {
 #define PIBM_EUNSTABLE (-4) /* non-finite fluid or particle state detected */
 #define PIBM_EESCAPED (-5)  /* a particle crossed a wall */
 #define PIBM_ENOTSUP (-6)   /* combination not built into this library */
+#define PIBM_EINTERNAL (-7) /* a device-side index check failed; the access was skipped */
 
 /* lattices (value = number of velocities q) */
 #define PIBM_D2Q9 9
@@ -166,6 +167,11 @@ int pibm_profile_steps(pibm_t* h, int64_t nsteps, double* phase_ms);
 void pibm_destroy(pibm_t* h);
 
 const char* pibm_strerror(int status);
+
+/* Text of the last failed CUDA call made by this library on the calling thread
+ * (name of the call, CUDA error name and description), or "" if none failed.
+ * The string stays valid until the next failing call on this thread. */
+const char* pibm_last_error(void);
 
 #ifdef __cplusplus
 }

@@ -17,6 +17,7 @@ PIBM_ECUDA = -3
 PIBM_EUNSTABLE = -4
 PIBM_EESCAPED = -5
 PIBM_ENOTSUP = -6
+PIBM_EINTERNAL = -7
 
 PIBM_D2Q9, PIBM_D3Q15, PIBM_D3Q19 = 9, 15, 19
 PIBM_WALL, PIBM_PERIODIC = 0, 1
@@ -29,7 +30,7 @@ NFIELDS = 5
 # every symbol include/pibm.h declares
 EXPORTS = ["pibm_workspace_bytes", "pibm_create", "pibm_step", "pibm_forces",
            "pibm_read_fields", "pibm_invariants", "pibm_status", "pibm_kernels_per_step",
-           "pibm_destroy", "pibm_strerror", "pibm_profile_steps"]
+           "pibm_destroy", "pibm_strerror", "pibm_profile_steps", "pibm_last_error"]
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -60,6 +61,8 @@ class PibmError(RuntimeError):
     def __init__(self, status, what=""):
         self.status = status
         msg = load().pibm_strerror(status).decode()
+        if status == PIBM_ECUDA:
+            msg += " [" + load().pibm_last_error().decode() + "]"
         super().__init__(f"{what}: {msg} (status {status})" if what else msg)
 
 
@@ -98,6 +101,8 @@ def load(path: str = LIB_PATH):
     L.pibm_destroy.restype = None
     L.pibm_strerror.argtypes = [ctypes.c_int]
     L.pibm_strerror.restype = ctypes.c_char_p
+    L.pibm_last_error.argtypes = []
+    L.pibm_last_error.restype = ctypes.c_char_p
     _lib = L
     return L
 

@@ -2,6 +2,7 @@
 // layout, upload of the initial state, the step loop (replayed from CUDA graphs
 // of two steps) and the read-back calls.
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -24,6 +25,7 @@ struct pibm_t {
   int graph_failed;
   double* out_dev;         // small device scratch for reductions
   int kernels_per_step;
+  int debug_sync;          // synchronise after every phase (PIBM_DEBUG_SYNC=1)
 };
 
 namespace {
@@ -33,7 +35,7 @@ constexpr size_t ALIGN = 256;
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-  size_t f, F, red, err, out, X, U, rad, mass, Ap, buoy, gw, radf, xf, g, Fc, key, rank, perm, bin,
+  size_t f, F, mom, red, err, out, X, U, rad, mass, Ap, buoy, gw, radf, xr, xs, g, Fc, key, rank, perm, bin,
       bsum;
   size_t total;
 };
@@ -121,7 +123,8 @@ Layout layout(const pibm_config* c) {
     return o;
   };
   L.f = take(2 * align_up((size_t)q * pitch * ts));
-  L.F = take((size_t)d * pitch * ts);
+  L.F = take((size_t)(d == 2 ? 2 : 4) * pitch * ts);
+  L.mom = take(c->n_particles > 0 ? (size_t)MOM_SLOTS * pitch * ts : 0);
   L.red = take(sizeof(double) * RED_SCRATCH);
   L.err = take(sizeof(unsigned));
   L.out = take(sizeof(double) * 8);
@@ -133,7 +136,8 @@ Layout layout(const pibm_config* c) {
   L.buoy = take(sizeof(double) * np);
   L.gw = take(sizeof(double) * np);
   L.radf = take(sizeof(float) * np);
-  L.xf = take(sizeof(float) * d * np);
+  L.xr = take(sizeof(float4) * np);
+  L.xs = take(sizeof(float4) * np);
   L.g = take(sizeof(double) * d * np);
   L.Fc = take(sizeof(double) * d * np);
   L.key = take(sizeof(unsigned) * np);
@@ -146,19 +150,39 @@ Layout layout(const pibm_config* c) {
 }
 
 
-#define CK(expr)                                   \
-  do {                                             \
-    cudaError_t e_ = (expr);                       \
-    if (e_ != cudaSuccess) return PIBM_ECUDA;      \
+// Description of the last failed CUDA call on this thread (pibm_last_error).
+thread_local char g_last_error[256] = "";
+
+void record_error(const char* what, cudaError_t e) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", what, cudaGetErrorName(e),
+           cudaGetErrorString(e));
+}
+
+#define CK(expr)                          \
+  do {                                    \
+    cudaError_t e_ = (expr);              \
+    if (e_ != cudaSuccess) {              \
+      record_error(#expr, e_);            \
+      return PIBM_ECUDA;                  \
+    }                                     \
+  } while (0)
+
+// With PIBM_DEBUG_SYNC=1 in the environment at pibm_create, steps are launched
+// without graphs and the stream is synchronised after every phase, so that an
+// error is attributed to the phase that raised it.
+#define PHASE(expr)                                        \
+  do {                                                     \
+    CK(expr);                                              \
+    if (h->debug_sync) CK(cudaStreamSynchronize(st));      \
   } while (0)
 
 int enqueue_step(pibm_t* h, cudaStream_t st) {
   State& s = h->s;
   int nk = 0;
-  CK(launch_bin(s, st, &nk));
-  CK(launch_contacts(s, st, &nk));
-  CK(launch_couple(s, st, &nk));
-  CK(launch_collide_stream(s, st));
+  PHASE(launch_bin(s, st, &nk));
+  PHASE(launch_contacts(s, st, &nk));
+  PHASE(launch_couple(s, st, &nk));
+  PHASE(launch_collide_stream(s, st));
   nk += 1;
   s.cur ^= 1;
   h->kernels_per_step = nk;
@@ -200,6 +224,7 @@ int health(pibm_t* h) {
   CK(cudaStreamSynchronize(h->stream));
   if (err & (ERR_FLUID_NONFINITE | ERR_PARTICLE_NONFINITE)) return PIBM_EUNSTABLE;
   if (err & ERR_ESCAPED) return PIBM_EESCAPED;
+  if (err & ERR_INDEX) return PIBM_EINTERNAL;
   return PIBM_OK;
 }
 
@@ -219,6 +244,8 @@ struct DeviceGuard {
 
 extern "C" {
 
+const char* pibm_last_error(void) { return g_last_error; }
+
 const char* pibm_strerror(int st) {
   switch (st) {
     case PIBM_OK: return "ok";
@@ -228,6 +255,7 @@ const char* pibm_strerror(int st) {
     case PIBM_EUNSTABLE: return "non-finite fluid or particle state";
     case PIBM_EESCAPED: return "a particle crossed a wall";
     case PIBM_ENOTSUP: return "configuration not supported by this build";
+    case PIBM_EINTERNAL: return "internal index check failed (access skipped)";
     default: return "unknown status";
   }
 }
@@ -255,6 +283,11 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
   memset(h, 0, sizeof(*h));
   cudaGetDevice(&h->device);
   h->stream = (cudaStream_t)stream;
+  {
+    const char* dbg = getenv("PIBM_DEBUG_SYNC");
+    h->debug_sync = dbg && dbg[0] == '1';
+    h->graph_failed = h->debug_sync;  // debug steps run eagerly
+  }
   if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
     delete h;
     return PIBM_ECUDA;
@@ -302,6 +335,7 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
   s.f[0] = base + L.f;
   s.f[1] = base + L.f + fbuf;
   s.F = base + L.F;
+  s.mom = base + L.mom;
   s.red = (double*)(base + L.red);
   s.err = (unsigned*)(base + L.err);
   h->out_dev = (double*)(base + L.out);
@@ -319,7 +353,8 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
   P.buoy = (double*)(base + L.buoy);
   P.gw = (double*)(base + L.gw);
   P.radf = (float*)(base + L.radf);
-  P.xf = (float*)(base + L.xf);
+  P.xr = (float4*)(base + L.xr);
+  P.xs = (float4*)(base + L.xs);
   P.g = (double*)(base + L.g);
   P.Fc = (double*)(base + L.Fc);
   P.key = (unsigned*)(base + L.key);
@@ -338,7 +373,7 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
     return code;
   };
   // force field and health word start at zero
-  if (cudaMemsetAsync(s.F, 0, (size_t)d * s.geo.pitch * ts, st) != cudaSuccess ||
+  if (cudaMemsetAsync(s.F, 0, (size_t)(d == 2 ? 2 : 4) * s.geo.pitch * ts, st) != cudaSuccess ||
       cudaMemsetAsync(s.err, 0, sizeof(unsigned), st) != cudaSuccess)
     return fail(PIBM_ECUDA);
 
@@ -405,7 +440,7 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
       return fail(PIBM_ECUDA);
   }
   if (cudaStreamSynchronize(st) != cudaSuccess) return fail(PIBM_ECUDA);
-  h->kernels_per_step = np > 0 ? (s.deterministic ? 10 : 9) : 1;
+  h->kernels_per_step = np > 0 ? (s.deterministic ? 11 : 9) : 1;
   *out = h;
   return PIBM_OK;
 }

@@ -81,16 +81,16 @@ __global__ void __launch_bounds__(256) k_collide_stream(const typename St::T* __
 
   // force of this step, consumed here and cleared for the next spread
   R Fv[3] = {R(0), R(0), R(0)};
-  bool any = false;
+  {
+    FT v[3];
+    load_force<D, FT>(F, c, v);
+    bool any = false;
 #pragma unroll
-  for (int k = 0; k < D; ++k) {
-    FT v = F[k * P + c];
-    any |= nonzero_bits(v);
-    Fv[k] = (R)v;
-  }
-  if (any) {
-#pragma unroll
-    for (int k = 0; k < D; ++k) F[k * P + c] = FT(0);
+    for (int k = 0; k < D; ++k) {
+      any |= nonzero_bits(v[k]);
+      Fv[k] = (R)v[k];
+    }
+    if (any) clear_force<D, FT>(F, c);
   }
 
   // moments: sum of stored values and first moment

@@ -10,6 +10,7 @@
 //     (Eqs. 6-7) and spreads A_p g back to the lattice (Eq. 9).
 // Particle state is FP64 structure-of-arrays; positions and velocities are
 // double-buffered so that every contact reads the state of step n.
+#include <limits.h>
 #include <math.h>
 
 #include "pibm_internal.cuh"
@@ -43,17 +44,20 @@ __device__ __forceinline__ unsigned bin_index(const BinMap& b, int x, int y, int
 // contiguous bin range, so after sorting its particles form one contiguous range.
 template <int D>
 __global__ void k_bin_key(const double* __restrict__ X, long long np, Geometry g, BinMap bm,
-                          unsigned* __restrict__ key, unsigned* __restrict__ rank,
-                          unsigned* __restrict__ cnt, float* __restrict__ xf) {
+                          const float* __restrict__ radf, unsigned* __restrict__ key,
+                          unsigned* __restrict__ rank, unsigned* __restrict__ cnt,
+                          float4* __restrict__ xr) {
   long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= np) return;
   int b[3] = {0, 0, 0};
+  float xf[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     const double x = X[k * np + p];
     b[k] = bin_coord(x, g.n[k]);
-    xf[k * np + p] = (float)x;
+    xf[k] = (float)x;
   }
+  xr[p] = make_float4(xf[0], xf[1], xf[2], radf[p]);
   unsigned kk = bin_index<D>(bm, b[0], b[1], b[2]);
   key[p] = kk;
   rank[p] = atomicAdd(&cnt[kk], 1u);
@@ -158,15 +162,19 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(unsigned* __restrict
 // the contact sums run in a fixed order.
 __global__ void k_bin_scatter(const unsigned* __restrict__ key, const unsigned* __restrict__ rank,
                               const unsigned* __restrict__ start, long long np,
-                              unsigned* __restrict__ perm) {
+                              const float4* __restrict__ xr, unsigned* __restrict__ perm,
+                              float4* __restrict__ xs) {
   long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= np) return;
-  perm[start[key[p]] + rank[p]] = (unsigned)p;
+  const unsigned sl = start[key[p]] + rank[p];
+  perm[sl] = (unsigned)p;
+  xs[sl] = xr[p];  // FP32 position and radius in sorted order (contact pre-filter)
 }
 
 __global__ void k_bin_sort(const unsigned* __restrict__ key, const unsigned* __restrict__ rank,
                            const unsigned* __restrict__ start, long long np,
-                           unsigned* __restrict__ perm) {
+                           const float4* __restrict__ xr, unsigned* __restrict__ perm,
+                           float4* __restrict__ xs) {
   long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= np || rank[p] != 0u) return;
   unsigned b = key[p];
@@ -180,6 +188,7 @@ __global__ void k_bin_sort(const unsigned* __restrict__ key, const unsigned* __r
     }
     perm[j] = v;
   }
+  for (unsigned i = lo; i < hi; ++i) xs[i] = xr[perm[i]];
 }
 
 // ---------------------------------------------------------------------------
@@ -310,13 +319,14 @@ struct CoupleArgs {
   const double* buoy;
   const double* gw;     // wall damping coefficient per particle
   const float* radf;    // radius (FP32)
-  const float* xf;      // [d][np] FP32 positions of step n
+  const float4* xs;     // [np] FP32 position and radius of step n, sorted order
   float xf_margin;      // bound on the FP32 rounding error of a distance
   double* gout;      // [d][np]
   double* Fcout;     // [d][np]
   const unsigned* perm;
   const unsigned* start;
   const void* f;     // stored populations f*
+  const void* mom;   // moment field (k_moments)
   void* F;           // force field
   unsigned* err;
   int spread;        // 1: spread A_p g into F (through the tile's shared-memory copy)
@@ -337,15 +347,17 @@ __global__ void __launch_bounds__(256) k_contacts(CoupleArgs A) {
   const BinMap& bm = A.bm;
   const long long np = A.np;
   const unsigned p = A.perm[sl];
+  if (p >= (unsigned)np) {
+    atomicOr(A.err, ERR_INDEX);
+    return;
+  }
   const float mrg = A.xf_margin;
-  float xp[3] = {0.f, 0.f, 0.f};
+  const float4 me = A.xs[sl];
+  const float xp[3] = {me.x, me.y, me.z};
+  const float rpf = me.w;
   int bc[3] = {0, 0, 0};
 #pragma unroll
-  for (int k = 0; k < D; ++k) {
-    xp[k] = A.xf[k * np + p];
-    bc[k] = bin_coord(A.X[k * np + p], g.n[k]);
-  }
-  const float rpf = A.radf[p];
+  for (int k = 0; k < D; ++k) bc[k] = bin_coord(A.X[k * np + p], g.n[k]);
   double Fc[3] = {0.0, 0.0, 0.0};
 #pragma unroll 1
   for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz) {
@@ -355,19 +367,37 @@ __global__ void __launch_bounds__(256) k_contacts(CoupleArgs A) {
     for (int oy = -1; oy <= 1; ++oy) {
       int cy = bc[1] + oy;
       if (!lattice_coord(cy, g.n[1], g.periodic[1])) continue;
-#pragma unroll 1
+      // the cells x-1, x, x+1 of this row, as runs of consecutive bins
+      unsigned runs[3][2];
+      int nrun = 0;
+#pragma unroll
       for (int ox = -1; ox <= 1; ++ox) {
         int cx = bc[0] + ox;
         if (!lattice_coord(cx, g.n[0], g.periodic[0])) continue;
         const unsigned b = bin_index<D>(bm, cx, cy, cz);
-        const unsigned lo = A.start[b], hi = A.start[b + 1];
+        if (nrun > 0 && runs[nrun - 1][1] == b) {
+          runs[nrun - 1][1] = b + 1;
+        } else {
+          runs[nrun][0] = b;
+          runs[nrun][1] = b + 1;
+          ++nrun;
+        }
+      }
+#pragma unroll 1
+      for (int r = 0; r < nrun; ++r) {
+        const unsigned lo = A.start[runs[r][0]], hi = A.start[runs[r][1]];
+        if (hi > (unsigned)np || lo > hi) {
+          atomicOr(A.err, ERR_INDEX);
+          continue;
+        }
         for (unsigned s2 = lo; s2 < hi; ++s2) {
-          const unsigned q = A.perm[s2];
-          if (q == p) continue;
+          if (s2 == (unsigned)sl) continue;
+          const float4 o = A.xs[s2];
+          const float oq[3] = {o.x, o.y, o.z};
           float d2f = 0.f;
 #pragma unroll
           for (int k = 0; k < D; ++k) {
-            float s = xp[k] - A.xf[k * np + q];
+            float s = xp[k] - oq[k];
             if (g.periodic[k]) {
               const float N = (float)g.n[k];
               if (s > 0.5f * N) s -= N;
@@ -375,9 +405,14 @@ __global__ void __launch_bounds__(256) k_contacts(CoupleArgs A) {
             }
             d2f += s * s;
           }
-          const float reach = rpf + A.radf[q] + mrg;
+          const float reach = rpf + o.w + mrg;
           if (d2f > reach * reach) continue;
+          const unsigned q = A.perm[s2];
           // FP64 overlap test and force
+          if (q >= (unsigned)np) {
+            atomicOr(A.err, ERR_INDEX);
+            continue;
+          }
           double X[3], s[3], d2 = 0.0;
 #pragma unroll
           for (int k = 0; k < D; ++k) {
@@ -419,109 +454,127 @@ __global__ void __launch_bounds__(256) k_contacts(CoupleArgs A) {
   for (int k = 0; k < D; ++k) A.Fcout[k * np + p] = Fc[k];
 }
 
-template <int D, int W>
-struct TileShape {
-  static constexpr int H = W / 2;  // halo: the stencil of a particle in a tile cell
-  static constexpr int TX = TileDims<D>::TX, TY = TileDims<D>::TY, TZ = TileDims<D>::TZ;
-  static constexpr int RX = TX + 2 * H, RY = TY + 2 * H, RZ = D == 2 ? 1 : TZ + 2 * H;
-  static constexpr int RC = RX * RY * RZ;
-};
-
-// One CTA per tile of lattice cells (tile-major bins make its particles one
-// contiguous range of the sorted list):
-//  1. the post-stream moments of every cell of the tile plus a halo of W/2
-//     cells (every node a particle of the tile can touch) go to shared memory;
-//  2. each particle of the tile interpolates from them, sums its contacts,
-//     advances, forms g and spreads A_p g w into a shared-memory copy of F over
-//     the same region;
-//  3. the region's non-zero F entries are added to the global field.
-// Tiles without particles return at once.
-template <int Q, int W, class St, typename FT>
-__global__ void __launch_bounds__(128) k_couple(CoupleArgs A) {
+// Post-stream moments of every cell of the tiles that hold particles or touch
+// a tile that does (the 2-cell delta stencil never reaches further), one CTA per
+// tile of TileDims cells: mom[0] = sum of stored values (rho - S), mom[1..d] = j.
+// Cells of other tiles are left untouched; no stencil reads them.
+template <int Q, class St>
+__global__ void __launch_bounds__(256) k_moments(Geometry g, BinMap bm,
+                                                 const unsigned* __restrict__ start,
+                                                 const typename St::T* __restrict__ f,
+                                                 typename St::R* __restrict__ mom) {
   using L = Lattice<Q>;
-  using T = typename St::T;
   using R = typename St::R;
   constexpr int D = L::D;
-  using TS = TileShape<D, W>;
-  constexpr int RX = TS::RX, RY = TS::RY, RC = TS::RC;
-  const Geometry& g = A.g;
-  const BinMap& bm = A.bm;
-  const unsigned tile = blockIdx.x;
-  const unsigned p0 = A.start[tile * (unsigned)bm.tc];
-  const unsigned p1 = A.start[(tile + 1) * (unsigned)bm.tc];
-  if (p0 == p1) return;
-  const int t0 = tile % bm.nt[0], t1 = (tile / bm.nt[0]) % bm.nt[1];
-  const int t2 = tile / (bm.nt[0] * bm.nt[1]);
-  const int o0 = t0 * TS::TX - TS::H, o1 = t1 * TS::TY - TS::H;
-  const int o2 = D == 3 ? t2 * TS::TZ - TS::H : 0;
-
-  extern __shared__ __align__(16) unsigned char smraw[];
-  R* mom = (R*)smraw;                                  // [D + 1][RC]
-  FT* Fs = (FT*)(smraw + sizeof(R) * (D + 1) * RC);   // [D][RC]
-  const T* f = (const T*)A.f;
-
-  for (int i = threadIdx.x; i < RC; i += blockDim.x) {
-    int x = o0 + i % RX, y = o1 + (i / RX) % RY, z = o2 + i / (RX * RY);
-    R r = R(0), j[3] = {R(0), R(0), R(0)};
-    if (lattice_coord(x, g.n[0], g.periodic[0]) && lattice_coord(y, g.n[1], g.periodic[1]) &&
-        lattice_coord(z, g.n[2], g.periodic[2]))
-      pull_moments<Q, St>(f, g, x, y, z, r, j);
-    mom[i] = r;
+  using TD = TileDims<D>;
+  const int tile = blockIdx.x;
+  const int t[3] = {tile % bm.nt[0], (tile / bm.nt[0]) % bm.nt[1], tile / (bm.nt[0] * bm.nt[1])};
+  int busy = 0;
+  if (threadIdx.x < (D == 3 ? 27 : 9)) {
+    const int o[3] = {(int)threadIdx.x % 3 - 1, ((int)threadIdx.x / 3) % 3 - 1,
+                      D == 3 ? (int)threadIdx.x / 9 - 1 : 0};
+    int nb[3];
+    bool ok = true;
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-      mom[(k + 1) * RC + i] = j[k];
-      Fs[k * RC + i] = FT(0);
+    for (int k = 0; k < 3; ++k) {
+      nb[k] = t[k] + o[k];
+      if (nb[k] < 0 || nb[k] >= bm.nt[k]) {
+        if (g.periodic[k]) nb[k] = (nb[k] + bm.nt[k]) % bm.nt[k];
+        else ok = false;
+      }
+    }
+    if (ok) {
+      const unsigned nt = (unsigned)(nb[0] + bm.nt[0] * (nb[1] + bm.nt[1] * nb[2]));
+      busy = start[(nt + 1) * (unsigned)TD::TC] != start[nt * (unsigned)TD::TC];
     }
   }
-  __syncthreads();
+  if (!__syncthreads_or(busy)) return;
+  for (int i = threadIdx.x; i < TD::TC; i += blockDim.x) {
+    const int x = t[0] * TD::TX + i % TD::TX;
+    const int y = t[1] * TD::TY + (i / TD::TX) % TD::TY;
+    const int z = t[2] * TD::TZ + i / (TD::TX * TD::TY);
+    if (x >= g.n[0] || y >= g.n[1] || z >= g.n[2]) continue;
+    R r, j[3];
+    pull_moments<Q, St>(f, g, x, y, z, r, j);
+    const long long c = x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
+    store_moments<R>(mom, c, r, j);
+  }
+}
 
+// Particle coupling, one thread per particle in cell-sorted order: interpolate
+// rho, j from the moment field with the delta weights (Eq. 4), take the contact
+// force (k_contacts), advance U and X (Eq. 13), form g = 2 (rho_l U - j_l)
+// (Eqs. 6-7) and spread A_p g w into F (Eq. 9).
+// Spreading adds each tap with one vector atomic per cell (FP32) or one atomic
+// per component (FP64); the cell-sorted order keeps a warp's taps close together.
+template <int Q, int W, class St, typename FT>
+__global__ void __launch_bounds__(256) k_couple(CoupleArgs A) {
+  using L = Lattice<Q>;
+  using R = typename St::R;
+  constexpr int D = L::D;
+  constexpr int WZ = D == 3 ? W : 1;
+  const long long sl = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const Geometry& g = A.g;
   const long long np = A.np;
-  for (unsigned sl = p0 + threadIdx.x; sl < p1; sl += blockDim.x) {
-    const unsigned p = A.perm[sl];
-    double X[3] = {0.0, 0.0, 0.0}, U[3] = {0.0, 0.0, 0.0};
+  Taps<W, R> tx, ty, tz;
+  FT amp[3] = {FT(0), FT(0), FT(0)};
+  bool act = sl < A.np;
+  unsigned p = 0;
+  if (act) {
+    p = A.perm[sl];
+    if (p >= (unsigned)np) {
+      atomicOr(A.err, ERR_INDEX);
+      act = false;
+    }
+  }
+  if (act) {
+    double X[3] = {0.0, 0.0, 0.0}, U[3] = {0.0, 0.0, 0.0}, Fc[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       X[k] = A.X[k * np + p];
       U[k] = A.U[k * np + p];
+      Fc[k] = A.Fcout[k * np + p];
     }
-    // --- interpolation of rho, j (Eq. 4) from the staged moments ---
-    Taps<W, R> tx, ty, tz;
+    const double mi = A.mass[p], Ap = A.Ap[p], bu = A.buoy[p];
+    const R* mom = (const R*)A.mom;
+
+    // --- interpolation of rho, j (Eq. 4) ---
     axis_taps<W, R>(X[0], g.n[0], g.periodic[0], tx);
     axis_taps<W, R>(X[1], g.n[1], g.periodic[1], ty);
     if constexpr (D == 3) axis_taps<W, R>(X[2], g.n[2], g.periodic[2], tz);
-    const int lx0 = tx.first - o0, ly0 = ty.first - o1;
-    int lz0 = 0;
-    if constexpr (D == 3) lz0 = tz.first - o2;
     R rs = R(0), js[3] = {R(0), R(0), R(0)};
-    constexpr int WZ = D == 3 ? W : 1;
 #pragma unroll 1
     for (int iz = 0; iz < WZ; ++iz) {
       R wz = R(1);
-      if constexpr (D == 3) wz = tz.w[iz];
+      long long zoff = 0;
+      if constexpr (D == 3) {
+        wz = tz.w[iz];
+        zoff = (long long)tz.idx[iz] * g.n[1];
+      }
+      if (wz == R(0)) continue;
 #pragma unroll
       for (int iy = 0; iy < W; ++iy) {
         const R wyz = ty.w[iy] * wz;
-        const int row = ((lz0 + iz) * RY + (ly0 + iy)) * RX + lx0;
+        const long long row = (zoff + ty.idx[iy]) * g.n[0];
 #pragma unroll
         for (int ix = 0; ix < W; ++ix) {
           const R wt = tx.w[ix] * wyz;
-          rs += wt * mom[row + ix];
+          R m[4];
+          if (row + tx.idx[ix] < 0 || row + tx.idx[ix] >= g.ncell) {
+            atomicOr(A.err, ERR_INDEX);
+            continue;
+          }
+          load_moments<R>(mom, row + tx.idx[ix], m);
+          rs += wt * m[0];
 #pragma unroll
-          for (int k = 0; k < D; ++k) js[k] += wt * mom[(k + 1) * RC + row + ix];
+          for (int k = 0; k < D; ++k) js[k] += wt * m[k + 1];
         }
       }
     }
     const double rho_l = (double)St::S + (double)rs;
     double j_l[3] = {(double)js[0], (double)js[1], (double)js[2]};
 
-    // --- contact force of this step (k_contacts) ---
-    const double mi = A.mass[p];
-    double Fc[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-    for (int k = 0; k < D; ++k) Fc[k] = A.Fcout[k * np + p];
-
     // --- particle update (Eq. 13) and force density (Eqs. 6-7) ---
-    const double Ap = A.Ap[p], bu = A.buoy[p];
     double Un[3], Ub[3], gg[3];
     if (A.ph.implicit_drag) {
       const double inv = 1.0 / (mi + 2.0 * Ap * rho_l);
@@ -539,7 +592,6 @@ __global__ void __launch_bounds__(128) k_couple(CoupleArgs A) {
       }
     }
     bool bad = false, esc = false;
-    FT amp[3];
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       gg[k] = 2.0 * (rho_l * Ub[k] - j_l[k]);
@@ -561,47 +613,32 @@ __global__ void __launch_bounds__(128) k_couple(CoupleArgs A) {
     }
     if (bad) atomicOr(A.err, ERR_PARTICLE_NONFINITE);
     if (esc) atomicOr(A.err, ERR_ESCAPED);
+  }
 
-    // --- spreading (Eq. 9) into the shared-memory copy of F ---
-    if (A.spread) {
+  // --- spreading (Eq. 9) ---
+  if (!A.spread || !act) return;
+  FT* F = (FT*)A.F;
 #pragma unroll 1
-      for (int iz = 0; iz < WZ; ++iz) {
-        FT wz = FT(1);
-        if constexpr (D == 3) wz = (FT)tz.w[iz];
+  for (int iz = 0; iz < WZ; ++iz) {
+    FT wz = FT(1);
+    long long zoff = 0;
+    if constexpr (D == 3) {
+      wz = (FT)tz.w[iz];
+      zoff = (long long)tz.idx[iz] * g.n[1];
+    }
+    if (wz == FT(0)) continue;
 #pragma unroll
-        for (int iy = 0; iy < W; ++iy) {
-          const FT wyz = (FT)ty.w[iy] * wz;
-          const int row = ((lz0 + iz) * RY + (ly0 + iy)) * RX + lx0;
+    for (int iy = 0; iy < W; ++iy) {
+      const FT wyz = (FT)ty.w[iy] * wz;
+      const long long row = (zoff + ty.idx[iy]) * g.n[0];
 #pragma unroll
-          for (int ix = 0; ix < W; ++ix) {
-            const FT wt = (FT)tx.w[ix] * wyz;
-            if (wt == FT(0)) continue;
-#pragma unroll
-            for (int k = 0; k < D; ++k) atomicAdd(&Fs[k * RC + row + ix], amp[k] * wt);
-          }
-        }
+      for (int ix = 0; ix < W; ++ix) {
+        const FT wt = (FT)tx.w[ix] * wyz;
+        if (wt == FT(0)) continue;
+        FT v[3] = {amp[0] * wt, amp[1] * wt, amp[2] * wt};
+        add_force<D, FT>(F, row + tx.idx[ix], v);
       }
     }
-  }
-  if (!A.spread) return;
-  __syncthreads();
-  FT* F = (FT*)A.F;
-  for (int i = threadIdx.x; i < RC; i += blockDim.x) {
-    int x = o0 + i % RX, y = o1 + (i / RX) % RY, z = o2 + i / (RX * RY);
-    if (!(lattice_coord(x, g.n[0], g.periodic[0]) && lattice_coord(y, g.n[1], g.periodic[1]) &&
-          lattice_coord(z, g.n[2], g.periodic[2])))
-      continue;
-    FT v[3];
-    bool any = false;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      v[k] = Fs[k * RC + i];
-      any |= (v[k] != FT(0));
-    }
-    if (!any) continue;
-    const long long c = x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
-#pragma unroll
-    for (int k = 0; k < D; ++k) atomicAdd(&F[k * g.pitch + c], v[k]);
   }
 }
 
@@ -659,8 +696,7 @@ __global__ void __launch_bounds__(256) k_spread_gather(Geometry g, BinMap bm, lo
     }
   }
   const long long c = x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
-#pragma unroll
-  for (int k = 0; k < D; ++k) F[k * g.pitch + c] = acc[k];
+  store_force<D, FT>(F, c, acc);
 }
 
 __global__ void k_forces(long long np, int d, const double* __restrict__ Ap,
@@ -748,18 +784,24 @@ cudaError_t launch_bin(const State& s, cudaStream_t st, int* nk) {
   if (e != cudaSuccess) return e;
   const double* X = P.X[s.cur];
   if (s.geo.d == 2)
-    k_bin_key<2><<<blocks_for(P.np, 256), 256, 0, st>>>(X, P.np, s.geo, P.bm, P.key, P.rank,
-                                                        P.bin_cnt, P.xf);
+    k_bin_key<2><<<blocks_for(P.np, 256), 256, 0, st>>>(X, P.np, s.geo, P.bm, P.radf, P.key,
+                                                        P.rank, P.bin_cnt, P.xr);
   else
-    k_bin_key<3><<<blocks_for(P.np, 256), 256, 0, st>>>(X, P.np, s.geo, P.bm, P.key, P.rank,
-                                                        P.bin_cnt, P.xf);
+    k_bin_key<3><<<blocks_for(P.np, 256), 256, 0, st>>>(X, P.np, s.geo, P.bm, P.radf, P.key,
+                                                        P.rank, P.bin_cnt, P.xr);
   const long long n = P.nbin + 1;
   k_scan_reduce<<<P.scan_blocks, SCAN_THREADS, 0, st>>>(P.bin_cnt, n, P.block_sums);
   k_scan_top<<<1, SCAN_THREADS, 0, st>>>(P.block_sums, P.scan_blocks);
   k_scan_down<<<P.scan_blocks, SCAN_THREADS, 0, st>>>(P.bin_cnt, n, P.block_sums);
-  k_bin_scatter<<<blocks_for(P.np, 256), 256, 0, st>>>(P.key, P.rank, P.bin_cnt, P.np, P.perm);
-  k_bin_sort<<<blocks_for(P.np, 256), 256, 0, st>>>(P.key, P.rank, P.bin_cnt, P.np, P.perm);
-  if (nk) *nk += 6;
+  k_bin_scatter<<<blocks_for(P.np, 256), 256, 0, st>>>(P.key, P.rank, P.bin_cnt, P.np, P.xr,
+                                                       P.perm, P.xs);
+  if (nk) *nk += 5;
+  if (s.deterministic) {
+    // bins in particle-id order: every sum over a bin then runs in a fixed order
+    k_bin_sort<<<blocks_for(P.np, 256), 256, 0, st>>>(P.key, P.rank, P.bin_cnt, P.np, P.xr,
+                                                      P.perm, P.xs);
+    if (nk) *nk += 1;
+  }
   return cudaGetLastError();
 }
 
@@ -781,7 +823,7 @@ CoupleArgs couple_args(const State& s) {
   A.buoy = P.buoy;
   A.gw = P.gw;
   A.radf = P.radf;
-  A.xf = P.xf;
+  A.xs = P.xs;
   {
     // positions below 2^e round to FP32 within 2^(e-24) per coordinate
     int mx = s.geo.n[0] > s.geo.n[1] ? s.geo.n[0] : s.geo.n[1];
@@ -793,6 +835,7 @@ CoupleArgs couple_args(const State& s) {
   A.perm = P.perm;
   A.start = P.bin_cnt;
   A.f = s.f[s.cur];
+  A.mom = s.mom;
   A.F = s.F;
   A.err = s.err;
   A.spread = s.deterministic ? 0 : 1;
@@ -803,19 +846,14 @@ template <int Q, int W, class St, typename FT>
 cudaError_t couple_t(const State& s, cudaStream_t st, int* nk) {
   const Particles& P = s.p;
   constexpr int D = Lattice<Q>::D;
-  using TS = TileShape<D, W>;
-  constexpr size_t smem = sizeof(typename St::R) * (D + 1) * TS::RC + sizeof(FT) * D * TS::RC;
-  static bool attr_set = false;  // per template instance; set before the first launch
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_couple<Q, W, St, FT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  using T = typename St::T;
+  using R = typename St::R;
   CoupleArgs A = couple_args(s);
   const unsigned ntiles = (unsigned)(P.nbin / P.bm.tc);
-  k_couple<Q, W, St, FT><<<ntiles, 128, smem, st>>>(A);
-  if (nk) *nk += 1;
+  k_moments<Q, St><<<ntiles, 256, 0, st>>>(s.geo, P.bm, P.bin_cnt, (const T*)s.f[s.cur],
+                                           (R*)s.mom);
+  k_couple<Q, W, St, FT><<<blocks_for(P.np, 256), 256, 0, st>>>(A);
+  if (nk) *nk += 2;
   if (s.deterministic) {
     const Geometry& g = s.geo;
     int bx = g.n[0] <= 32 ? 32 : (g.n[0] <= 64 ? 64 : 128);

@@ -76,11 +76,102 @@ struct StoreF32 {
   static constexpr int S = 1;
 };
 
+// Force and moment fields are cell-major: FSTRIDE force slots per cell (2 in 2D,
+// 4 in 3D with the last slot unused) and 4 moment slots per cell (rho - S, jx,
+// jy, jz), so that one vector access or one vector atomic moves a whole cell.
+template <int D>
+struct FieldStride {
+  static constexpr int F = D == 2 ? 2 : 4;
+};
+constexpr int MOM_SLOTS = 4;
+
+template <int D, typename FT>
+__device__ __forceinline__ void load_force(const FT* __restrict__ F, long long c, FT (&v)[3]) {
+  if constexpr (sizeof(FT) == 4 && D == 2) {
+    const float2 a = reinterpret_cast<const float2*>(F)[c];
+    v[0] = a.x; v[1] = a.y; v[2] = 0.f;
+  } else if constexpr (sizeof(FT) == 4) {
+    const float4 a = reinterpret_cast<const float4*>(F)[c];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z;
+  } else if constexpr (D == 2) {
+    const double2 a = reinterpret_cast<const double2*>(F)[c];
+    v[0] = a.x; v[1] = a.y; v[2] = 0.0;
+  } else {
+    const double2 a = reinterpret_cast<const double2*>(F)[2 * c];
+    const double2 b = reinterpret_cast<const double2*>(F)[2 * c + 1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x;
+  }
+}
+
+template <int D, typename FT>
+__device__ __forceinline__ void clear_force(FT* __restrict__ F, long long c) {
+  if constexpr (sizeof(FT) == 4 && D == 2) {
+    reinterpret_cast<float2*>(F)[c] = make_float2(0.f, 0.f);
+  } else if constexpr (sizeof(FT) == 4) {
+    reinterpret_cast<float4*>(F)[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+  } else if constexpr (D == 2) {
+    reinterpret_cast<double2*>(F)[c] = make_double2(0.0, 0.0);
+  } else {
+    reinterpret_cast<double2*>(F)[2 * c] = make_double2(0.0, 0.0);
+    reinterpret_cast<double2*>(F)[2 * c + 1] = make_double2(0.0, 0.0);
+  }
+}
+
+template <int D, typename FT>
+__device__ __forceinline__ void store_force(FT* __restrict__ F, long long c, const FT (&v)[3]) {
+  if constexpr (sizeof(FT) == 4 && D == 2) {
+    reinterpret_cast<float2*>(F)[c] = make_float2(v[0], v[1]);
+  } else if constexpr (sizeof(FT) == 4) {
+    reinterpret_cast<float4*>(F)[c] = make_float4(v[0], v[1], v[2], 0.f);
+  } else if constexpr (D == 2) {
+    reinterpret_cast<double2*>(F)[c] = make_double2(v[0], v[1]);
+  } else {
+    reinterpret_cast<double2*>(F)[2 * c] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(F)[2 * c + 1] = make_double2(v[2], 0.0);
+  }
+}
+
+// F(c) += v, atomically: one vector atomic per cell in FP32, one per component in FP64.
+template <int D, typename FT>
+__device__ __forceinline__ void add_force(FT* __restrict__ F, long long c, const FT (&v)[3]) {
+  if constexpr (sizeof(FT) == 4 && D == 2) {
+    atomicAdd(reinterpret_cast<float2*>(F) + c, make_float2(v[0], v[1]));
+  } else if constexpr (sizeof(FT) == 4) {
+    atomicAdd(reinterpret_cast<float4*>(F) + c, make_float4(v[0], v[1], v[2], 0.f));
+  } else {
+#pragma unroll
+    for (int k = 0; k < D; ++k) atomicAdd(F + (long long)FieldStride<D>::F * c + k, v[k]);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void load_moments(const R* __restrict__ mom, long long c, R (&m)[4]) {
+  if constexpr (sizeof(R) == 4) {
+    const float4 a = reinterpret_cast<const float4*>(mom)[c];
+    m[0] = a.x; m[1] = a.y; m[2] = a.z; m[3] = a.w;
+  } else {
+    const double2 a = reinterpret_cast<const double2*>(mom)[2 * c];
+    const double2 b = reinterpret_cast<const double2*>(mom)[2 * c + 1];
+    m[0] = a.x; m[1] = a.y; m[2] = b.x; m[3] = b.y;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void store_moments(R* __restrict__ mom, long long c, R r, const R (&j)[3]) {
+  if constexpr (sizeof(R) == 4) {
+    reinterpret_cast<float4*>(mom)[c] = make_float4(r, j[0], j[1], j[2]);
+  } else {
+    reinterpret_cast<double2*>(mom)[2 * c] = make_double2(r, j[0]);
+    reinterpret_cast<double2*>(mom)[2 * c + 1] = make_double2(j[1], j[2]);
+  }
+}
+
 // Device health flags (bitwise OR into State::err).
 enum : unsigned {
   ERR_FLUID_NONFINITE = 1u,
   ERR_PARTICLE_NONFINITE = 2u,
   ERR_ESCAPED = 4u,
+  ERR_INDEX = 8u,  // an internal index check failed; the access was skipped
 };
 
 // ---------------------------------------------------------------------------
@@ -128,7 +219,8 @@ struct Particles {
   double* buoy;   // mass * (1 - 1 / rho_r)
   double* gw;     // wall damping coefficient 2 beta sqrt(mass kn)
   float* radf;    // radius in FP32 (contact pre-filter)
-  float* xf;      // [d][np] positions in FP32 (contact pre-filter), written by binning
+  float4* xr;     // [np] FP32 position and radius by particle id (written by binning)
+  float4* xs;     // [np] the same in sorted order (contact pre-filter)
   double* g;      // [d][np] force density of the last step (Eq. 7)
   double* Fc;     // [d][np] contact force of the last step
   // cell list (bins = lattice cells)
@@ -148,7 +240,8 @@ struct State {
   int precision;
   int deterministic;
   void* f[2];     // population buffers (post-collision of the last step), [q][pitch]
-  void* F;        // force field [d][pitch], double (FP64) or float (FP32)
+  void* F;        // force field [pitch][FieldStride], double (FP64) or float (FP32)
+  void* mom;      // moment field [pitch][4] of the current state (cells near particles)
   double* red;    // reduction scratch
   unsigned* err;  // device health word
   Particles p;

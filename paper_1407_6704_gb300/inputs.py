@@ -78,16 +78,19 @@ def _draw(rng, spec, n):
 
 
 def sample_particles(n: Sequence[int], n_particles: int, diameter, density_ratio,
-                     band=(0.5, 1.0), seed=0, slots=None, max_rounds=400):
+                     band=(0.5, 1.0), seed=0, max_rounds=400):
     """Uniform random, pairwise non-overlapping particles.
 
     Positions are drawn uniformly in a box that keeps every particle at least
     half the largest diameter away from each face of the domain; along the last
     axis (the gravity axis) the box is further restricted to ``band`` (fractions
-    of the extent). A candidate is kept when it overlaps no kept particle; within
-    one round of candidates the lower index wins. Returns X (np, d), diameter (np,),
-    density ratio (np,), all float64.
+    of the extent). Every round draws positions for the particles not yet placed;
+    a candidate is kept when it overlaps no kept particle and no lower-index
+    candidate of the same round. Returns X (np, d), diameter (np,), density ratio
+    (np,), all float64.
     """
+    from scipy.spatial import cKDTree
+
     rng = np.random.Generator(np.random.PCG64(seed))
     d = len(n)
     dia = _draw(rng, diameter, n_particles)
@@ -95,94 +98,56 @@ def sample_particles(n: Sequence[int], n_particles: int, diameter, density_ratio
     if n_particles == 0:
         return np.zeros((0, d)), dia, rr
     dmax = float(dia.max())
-    cs = max(1.0, float(np.ceil(dmax)))  # grid cell size >= largest contact distance
     lo = np.full(d, 0.5 * dmax)
     hi = np.array(n, dtype=np.float64) - 0.5 * dmax
     lo[-1] = max(lo[-1], band[0] * n[-1])
     hi[-1] = min(hi[-1], band[1] * n[-1])
     if np.any(hi <= lo):
         raise ValueError("empty placement region")
-    gdim = np.ceil(np.array(n, dtype=np.float64) / cs).astype(np.int64)
-    ngc = int(np.prod(gdim))
-    K = slots or (6 if d == 2 else 4)
-    grid = np.full((ngc, K), -1, dtype=np.int32)
-    fill = np.zeros(ngc, dtype=np.int64)
     X = np.zeros((n_particles, d))
     placed = np.zeros(n_particles, dtype=bool)
-    offs = np.array(np.meshgrid(*([[-1, 0, 1]] * d), indexing="ij")).reshape(d, -1).T
-
-    def gcoord(P):
-        return np.minimum((P / cs).astype(np.int64), gdim - 1)
-
-    def flat(gc):
-        idx = gc[:, -1]
-        for k in range(d - 2, -1, -1):
-            idx = idx * gdim[k] + gc[:, k]
-        return idx
-
+    # kept particles live in a large tree rebuilt rarely plus a small recent set
+    base_ids = np.zeros(0, dtype=np.int64)
+    base_tree = None
+    recent = []
     for _ in range(max_rounds):
         todo = np.nonzero(~placed)[0]
         if todo.size == 0:
             break
         cand = lo + (hi - lo) * rng.random((todo.size, d))
-        gc = gcoord(cand)
         ok = np.ones(todo.size, dtype=bool)
-        # against particles already kept
-        for o in offs:
-            nb = gc + o
-            inside = np.all((nb >= 0) & (nb < gdim), axis=1)
-            nbf = flat(np.where(inside[:, None], nb, 0))
-            for s in range(K):
-                other = grid[nbf, s]
-                valid = inside & (other >= 0)
-                if not valid.any():
-                    continue
-                oi = np.where(valid, other, 0)
-                dist = np.linalg.norm(cand - X[oi], axis=1)
-                clash = valid & (dist < 0.5 * (dia[todo] + dia[oi]))
-                ok &= ~clash
-        # within this round: lower index wins
+        # against the particles already kept
+        rec = np.concatenate(recent) if recent else np.zeros(0, dtype=np.int64)
+        if rec.size > max(base_ids.size // 4, 1024):
+            base_ids = np.concatenate([base_ids, rec])
+            base_tree = cKDTree(X[base_ids])
+            recent, rec = [], np.zeros(0, dtype=np.int64)
+        ctree = None
+        for ids, tree in ((base_ids, base_tree), (rec, None)):
+            if ids.size == 0:
+                continue
+            if tree is None:
+                tree = cKDTree(X[ids])
+            if ctree is None:
+                ctree = cKDTree(cand)
+            pairs = ctree.sparse_distance_matrix(tree, dmax, output_type="ndarray")
+            if pairs.size:
+                ci, ki, dist = pairs["i"], pairs["j"], pairs["v"]
+                clash = dist < 0.5 * (dia[todo[ci]] + dia[ids[ki]])
+                ok[ci[clash]] = False
+        # within the round: the lower index wins
         sel = np.nonzero(ok)[0]
-        if sel.size:
-            cf = flat(gc[sel])
-            order = np.lexsort((sel, cf))
-            sc = cf[order]
-            ss = sel[order]
-            start = np.searchsorted(sc, sc, side="left")
-            rank = np.arange(sc.size) - start
-            Kt = int(rank.max()) + 1
-            tmp = np.full((ngc, Kt), -1, dtype=np.int32)
-            tmp[sc, rank] = ss
-            for o in offs:
-                nb = gc[sel] + o
-                inside = np.all((nb >= 0) & (nb < gdim), axis=1)
-                nbf = flat(np.where(inside[:, None], nb, 0))
-                for s in range(Kt):
-                    other = tmp[nbf, s]
-                    valid = inside & (other >= 0) & (other < sel)
-                    if not valid.any():
-                        continue
-                    oi = np.where(valid, other, 0)
-                    dist = np.linalg.norm(cand[sel] - cand[oi], axis=1)
-                    clash = valid & (dist < 0.5 * (dia[todo[sel]] + dia[todo[oi]]))
-                    ok[sel[clash]] = False
-        # insert the survivors, respecting the per-cell slot limit
+        if sel.size > 1:
+            pr = cKDTree(cand[sel]).query_pairs(dmax, output_type="ndarray")
+            if pr.size:
+                i, j = sel[pr.min(axis=1)], sel[pr.max(axis=1)]
+                dist = np.linalg.norm(cand[i] - cand[j], axis=1)
+                clash = dist < 0.5 * (dia[todo[i]] + dia[todo[j]])
+                ok[j[clash]] = False
         sel = np.nonzero(ok)[0]
-        if sel.size:
-            cf = flat(gc[sel])
-            order = np.lexsort((sel, cf))
-            sc = cf[order]
-            ss = sel[order]
-            start = np.searchsorted(sc, sc, side="left")
-            slot = fill[sc] + (np.arange(sc.size) - start)
-            keep = slot < K
-            sc, ss, slot = sc[keep], ss[keep], slot[keep]
-            pid = todo[ss]
-            grid[sc, slot] = pid
-            X[pid] = cand[ss]
-            placed[pid] = True
-            np.add.at(fill, sc, 1)
-            fill = np.minimum(fill, K)
+        X[todo[sel]] = cand[sel]
+        placed[todo[sel]] = True
+        recent.append(todo[sel])
     if not placed.all():
         raise RuntimeError(f"could not place {np.count_nonzero(~placed)} particles")
     return X, dia, rr
