@@ -57,6 +57,7 @@ extern "C" {
 #define PIBM_EESCAPED (-5)  /* a particle crossed a wall */
 #define PIBM_ENOTSUP (-6)   /* combination not built into this library */
 #define PIBM_EINTERNAL (-7) /* a device-side index check failed; the access was skipped */
+#define PIBM_ETOOBIG (-8)   /* larger than the fixed scratch of pibm_fluid_sums_noalloc */
 
 /* lattices (value = number of velocities q) */
 #define PIBM_D2Q9 9
@@ -167,6 +168,35 @@ int pibm_profile_steps(pibm_t* h, int64_t nsteps, double* phase_ms);
 void pibm_destroy(pibm_t* h);
 
 const char* pibm_strerror(int status);
+
+/* Total mass and fluid momentum of a population field held by the caller, with
+ * no device allocation of any kind (no cudaMalloc, cudaFree or allocating
+ * library routine). The paper has no counterpart; this is a service for callers
+ * that must not allocate device memory: code running inside a stream capture it
+ * does not own (an allocation there would break the capture or synchronise the
+ * device), real-time stepping loops held to a fixed memory budget, and
+ * allocator hooks that must not re-enter the allocator.
+ * f: device, [q][ncell] FP64 populations in the layout of PIBM_FIELD_POP, at
+ *   least q * ncell doubles; lattice: PIBM_D2Q9 / PIBM_D3Q15 / PIBM_D3Q19;
+ *   n: extents (n[2] = 1 for D2Q9); ncell = n[0] n[1] n[2].
+ * out: device, 1 + d doubles, written with sum_a f_a (total mass) and
+ *   sum_a e_a f_a (fluid momentum), summed in a fixed order (run to run
+ *   identical for the same input and size).
+ * stream: cudaStream_t to run on (NULL = legacy default stream); the call is
+ *   asynchronous and reports launch errors only.
+ * Limits and sharing: partial sums live in one file-scope static device array
+ *   of 128 KiB that every GPU loading this library holds until the process
+ *   exits; ncell may not exceed 16,777,216 (PIBM_ETOOBIG otherwise, nothing is
+ *   launched). All calls on a device share that array and keep the last call's
+ *   partials, so calls that overlap on the GPU (different streams without
+ *   ordering) race and give wrong sums; order them on one stream.
+ * The first call on each device looks up the array's device address with that
+ *   device current (cudaGetSymbolAddress); make that first call before any
+ *   stream capture that will contain later calls.
+ * Errors: PIBM_EINVAL (NULL pointer, bad lattice or extents), PIBM_ETOOBIG,
+ *   PIBM_ECUDA. */
+int pibm_fluid_sums_noalloc(const double* f, int lattice, const int64_t n[3], double* out,
+                            void* stream);
 
 /* Text of the last failed CUDA call made by this library on the calling thread
  * (name of the call, CUDA error name and description), or "" if none failed.

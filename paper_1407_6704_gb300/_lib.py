@@ -18,6 +18,7 @@ PIBM_EUNSTABLE = -4
 PIBM_EESCAPED = -5
 PIBM_ENOTSUP = -6
 PIBM_EINTERNAL = -7
+PIBM_ETOOBIG = -8
 
 PIBM_D2Q9, PIBM_D3Q15, PIBM_D3Q19 = 9, 15, 19
 PIBM_WALL, PIBM_PERIODIC = 0, 1
@@ -30,7 +31,8 @@ NFIELDS = 5
 # every symbol include/pibm.h declares
 EXPORTS = ["pibm_workspace_bytes", "pibm_create", "pibm_step", "pibm_forces",
            "pibm_read_fields", "pibm_invariants", "pibm_status", "pibm_kernels_per_step",
-           "pibm_destroy", "pibm_strerror", "pibm_profile_steps", "pibm_last_error"]
+           "pibm_destroy", "pibm_strerror", "pibm_profile_steps", "pibm_last_error",
+           "pibm_fluid_sums_noalloc"]
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -101,6 +103,8 @@ def load(path: str = LIB_PATH):
     L.pibm_destroy.restype = None
     L.pibm_strerror.argtypes = [ctypes.c_int]
     L.pibm_strerror.restype = ctypes.c_char_p
+    L.pibm_fluid_sums_noalloc.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), vp, vp]
+    L.pibm_fluid_sums_noalloc.restype = ctypes.c_int
     L.pibm_last_error.argtypes = []
     L.pibm_last_error.restype = ctypes.c_char_p
     _lib = L

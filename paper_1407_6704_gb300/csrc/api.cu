@@ -256,6 +256,7 @@ const char* pibm_strerror(int st) {
     case PIBM_EESCAPED: return "a particle crossed a wall";
     case PIBM_ENOTSUP: return "configuration not supported by this build";
     case PIBM_EINTERNAL: return "internal index check failed (access skipped)";
+    case PIBM_ETOOBIG: return "size exceeds the fixed static scratch of the no-allocation call";
     default: return "unknown status";
   }
 }

@@ -60,7 +60,7 @@ def test_config_struct_layout_matches_c(tmp_path):
 
 def test_strerror(lib):
     assert lib.pibm_strerror(0) == b"ok"
-    for st in range(-7, 0):
+    for st in range(-8, 0):
         assert lib.pibm_strerror(st) and lib.pibm_strerror(st) != b"unknown status"
 
 
