@@ -237,7 +237,9 @@ __device__ __forceinline__ void axis_taps(double X, int n, int periodic, Taps<W,
     for (int i = 0; i < W; ++i) {
       int k = t.first + i;
       bool in = (k >= 0 && k < n);
-      t.idx[i] = in ? k : 0;
+      // a dropped node keeps the nearest in-domain index: it lies next to the
+      // particle, so every field read there is one the step has written
+      t.idx[i] = in ? k : (k < 0 ? 0 : n - 1);
       if (!in) t.w[i] = WT(0);
       s += t.w[i];
     }
@@ -559,6 +561,7 @@ __global__ void __launch_bounds__(256) k_couple(CoupleArgs A) {
 #pragma unroll
         for (int ix = 0; ix < W; ++ix) {
           const R wt = tx.w[ix] * wyz;
+          if (wt == R(0)) continue;
           R m[4];
           if (row + tx.idx[ix] < 0 || row + tx.idx[ix] >= g.ncell) {
             atomicOr(A.err, ERR_INDEX);
