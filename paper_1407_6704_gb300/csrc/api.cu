@@ -35,7 +35,7 @@ constexpr size_t ALIGN = 256;
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-  size_t f, F, mom, red, err, out, X, U, rad, mass, Ap, buoy, gw, radf, xr, xs, g, Fc, key, rank, perm, bin,
+  size_t f, F, mom, red, err, out, X, U, rad, mass, Ap, buoy, gw, radf, xr, cr, xs, cs, g, Fc, key, rank, perm, bin,
       bsum;
   size_t total;
 };
@@ -137,7 +137,9 @@ Layout layout(const pibm_config* c) {
   L.gw = take(sizeof(double) * np);
   L.radf = take(sizeof(float) * np);
   L.xr = take(sizeof(float4) * np);
+  L.cr = take(sizeof(int4) * np);
   L.xs = take(sizeof(float4) * np);
+  L.cs = take(sizeof(int4) * np);
   L.g = take(sizeof(double) * d * np);
   L.Fc = take(sizeof(double) * d * np);
   L.key = take(sizeof(unsigned) * np);
@@ -355,7 +357,9 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
   P.gw = (double*)(base + L.gw);
   P.radf = (float*)(base + L.radf);
   P.xr = (float4*)(base + L.xr);
+  P.cr = (int4*)(base + L.cr);
   P.xs = (float4*)(base + L.xs);
+  P.cs = (int4*)(base + L.cs);
   P.g = (double*)(base + L.g);
   P.Fc = (double*)(base + L.Fc);
   P.key = (unsigned*)(base + L.key);

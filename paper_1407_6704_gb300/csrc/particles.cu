@@ -46,18 +46,19 @@ template <int D>
 __global__ void k_bin_key(const double* __restrict__ X, long long np, Geometry g, BinMap bm,
                           const float* __restrict__ radf, unsigned* __restrict__ key,
                           unsigned* __restrict__ rank, unsigned* __restrict__ cnt,
-                          float4* __restrict__ xr) {
+                          float4* __restrict__ xr, int4* __restrict__ cr) {
   long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= np) return;
   int b[3] = {0, 0, 0};
-  float xf[3] = {0.f, 0.f, 0.f};
+  float fr[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     const double x = X[k * np + p];
     b[k] = bin_coord(x, g.n[k]);
-    xf[k] = (float)x;
+    fr[k] = (float)(x - (double)b[k]);  // position inside its cell, exact to FP32
   }
-  xr[p] = make_float4(xf[0], xf[1], xf[2], radf[p]);
+  xr[p] = make_float4(fr[0], fr[1], fr[2], radf[p]);
+  cr[p] = make_int4(b[0], b[1], b[2], (int)p);
   unsigned kk = bin_index<D>(bm, b[0], b[1], b[2]);
   key[p] = kk;
   rank[p] = atomicAdd(&cnt[kk], 1u);
@@ -158,23 +159,29 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(unsigned* __restrict
   }
 }
 
-// Place each particle at its slot, then order every bin by particle id so that
-// the contact sums run in a fixed order.
+// Place each particle at its slot, together with its FP32 in-cell position and
+// radius (xs) and its cell and id (cs), which the contact and coupling kernels
+// read in slot order.
 __global__ void k_bin_scatter(const unsigned* __restrict__ key, const unsigned* __restrict__ rank,
                               const unsigned* __restrict__ start, long long np,
-                              const float4* __restrict__ xr, unsigned* __restrict__ perm,
-                              float4* __restrict__ xs) {
+                              const float4* __restrict__ xr, const int4* __restrict__ cr,
+                              unsigned* __restrict__ perm, float4* __restrict__ xs,
+                              int4* __restrict__ cs) {
   long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= np) return;
   const unsigned sl = start[key[p]] + rank[p];
   perm[sl] = (unsigned)p;
-  xs[sl] = xr[p];  // FP32 position and radius in sorted order (contact pre-filter)
+  xs[sl] = xr[p];
+  cs[sl] = cr[p];
 }
 
+// Deterministic mode: order every bin by particle id so that every sum over a
+// bin runs in a fixed order.
 __global__ void k_bin_sort(const unsigned* __restrict__ key, const unsigned* __restrict__ rank,
                            const unsigned* __restrict__ start, long long np,
-                           const float4* __restrict__ xr, unsigned* __restrict__ perm,
-                           float4* __restrict__ xs) {
+                           const float4* __restrict__ xr, const int4* __restrict__ cr,
+                           unsigned* __restrict__ perm, float4* __restrict__ xs,
+                           int4* __restrict__ cs) {
   long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= np || rank[p] != 0u) return;
   unsigned b = key[p];
@@ -188,7 +195,10 @@ __global__ void k_bin_sort(const unsigned* __restrict__ key, const unsigned* __r
     }
     perm[j] = v;
   }
-  for (unsigned i = lo; i < hi; ++i) xs[i] = xr[perm[i]];
+  for (unsigned i = lo; i < hi; ++i) {
+    xs[i] = xr[perm[i]];
+    cs[i] = cr[perm[i]];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -246,6 +256,72 @@ __device__ __forceinline__ void axis_taps(double X, int n, int periodic, Taps<W,
 #pragma unroll
     for (int i = 0; i < W; ++i) t.w[i] /= s;
   }
+}
+
+// The same taps from a particle's cell c and FP32 offset f inside it (X = c + f),
+// all in FP32 and integer arithmetic: floor(X - 1/2) = c + floor(f - 1/2) and
+// r_0 = (first - c) + 1/2 - f.
+template <int W>
+__device__ __forceinline__ void axis_taps_local(int c, float f, int n, int periodic,
+                                                Taps<W, float>& t) {
+  const int b = c + (int)floorf(f - 0.5f);
+  t.first = (W == 2) ? b : b - 1;
+  const float r0 = (float)(t.first - c) + 0.5f - f;
+  if constexpr (W == 2) {
+    t.w[0] = 1.f + r0;
+    t.w[1] = -r0;
+  } else {
+    float sn, cs;
+    sincospif(0.5f * r0, &sn, &cs);
+    t.w[0] = 0.25f * (1.f + cs);
+    t.w[1] = 0.25f * (1.f - sn);
+    t.w[2] = 0.25f * (1.f - cs);
+    t.w[3] = 0.25f * (1.f + sn);
+  }
+  if (periodic) {
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      int k = (t.first + i) % n;
+      t.idx[i] = k < 0 ? k + n : k;
+    }
+  } else {
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      int k = t.first + i;
+      bool in = (k >= 0 && k < n);
+      t.idx[i] = in ? k : (k < 0 ? 0 : n - 1);
+      if (!in) t.w[i] = 0.f;
+      s += t.w[i];
+    }
+#pragma unroll
+    for (int i = 0; i < W; ++i) t.w[i] /= s;
+  }
+}
+
+// 1/d in FP64 from an FP32 seed refined by Newton steps: one step gives about
+// 2^-46 relative error, two reach FP64 rounding.
+template <int STEPS>
+__device__ __forceinline__ double rcp_newton(double d) {
+  double r = (double)__frcp_rn((float)d);
+  if (!isfinite(r)) return 1.0 / d;
+#pragma unroll
+  for (int i = 0; i < STEPS; ++i) {
+    const double e = fma(-d, r, 1.0);
+    r = fma(r, e, r);
+  }
+  return r;
+}
+
+// Bit tests (integer pipe): not finite, and outside [0, n] for a wall axis.
+__device__ __forceinline__ bool not_finite_bits(double v) {
+  return ((unsigned long long)__double_as_longlong(v) & 0x7ff0000000000000ull) ==
+         0x7ff0000000000000ull;
+}
+__device__ __forceinline__ bool outside_bits(double v, double n) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return b > 0x8000000000000000ull ||  // negative and non-zero
+         (b < 0x8000000000000000ull && b > (unsigned long long)__double_as_longlong(n));
 }
 
 // Wrap a region coordinate onto the lattice: periodic axes wrap, wall axes
@@ -321,7 +397,8 @@ struct CoupleArgs {
   const double* buoy;
   const double* gw;     // wall damping coefficient per particle
   const float* radf;    // radius (FP32)
-  const float4* xs;     // [np] FP32 position and radius of step n, sorted order
+  const float4* xs;     // [np] FP32 in-cell position and radius of step n, sorted order
+  const int4* cs;       // [np] cell (x, y, z) and particle id, sorted order
   float xf_margin;      // bound on the FP32 rounding error of a distance
   double* gout;      // [d][np]
   double* Fcout;     // [d][np]
@@ -348,7 +425,8 @@ __global__ void __launch_bounds__(256) k_contacts(CoupleArgs A) {
   const Geometry& g = A.g;
   const BinMap& bm = A.bm;
   const long long np = A.np;
-  const unsigned p = A.perm[sl];
+  const int4 mc = A.cs[sl];
+  const unsigned p = (unsigned)mc.w;
   if (p >= (unsigned)np) {
     atomicOr(A.err, ERR_INDEX);
     return;
@@ -357,9 +435,7 @@ __global__ void __launch_bounds__(256) k_contacts(CoupleArgs A) {
   const float4 me = A.xs[sl];
   const float xp[3] = {me.x, me.y, me.z};
   const float rpf = me.w;
-  int bc[3] = {0, 0, 0};
-#pragma unroll
-  for (int k = 0; k < D; ++k) bc[k] = bin_coord(A.X[k * np + p], g.n[k]);
+  const int bc[3] = {mc.x, mc.y, mc.z};
   double Fc[3] = {0.0, 0.0, 0.0};
 #pragma unroll 1
   for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz) {
@@ -395,21 +471,24 @@ __global__ void __launch_bounds__(256) k_contacts(CoupleArgs A) {
         for (unsigned s2 = lo; s2 < hi; ++s2) {
           if (s2 == (unsigned)sl) continue;
           const float4 o = A.xs[s2];
+          const int4 oc = A.cs[s2];
           const float oq[3] = {o.x, o.y, o.z};
+          const int cq[3] = {oc.x, oc.y, oc.z};
           float d2f = 0.f;
 #pragma unroll
           for (int k = 0; k < D; ++k) {
-            float s = xp[k] - oq[k];
+            // whole cells apart (minimum image on periodic axes) plus the in-cell offsets
+            int dc = bc[k] - cq[k];
             if (g.periodic[k]) {
-              const float N = (float)g.n[k];
-              if (s > 0.5f * N) s -= N;
-              if (s < -0.5f * N) s += N;
+              if (2 * dc > g.n[k]) dc -= g.n[k];
+              if (2 * dc < -g.n[k]) dc += g.n[k];
             }
+            const float s = (float)dc + (xp[k] - oq[k]);
             d2f += s * s;
           }
           const float reach = rpf + o.w + mrg;
           if (d2f > reach * reach) continue;
-          const unsigned q = A.perm[s2];
+          const unsigned q = (unsigned)oc.w;
           // FP64 overlap test and force
           if (q >= (unsigned)np) {
             atomicOr(A.err, ERR_INDEX);
@@ -443,11 +522,12 @@ __global__ void __launch_bounds__(256) k_contacts(CoupleArgs A) {
   for (int k = 0; k < D; ++k) {
     if (g.periodic[k]) continue;
     const float nk = (float)g.n[k];
-    if (xp[k] < rpf + mrg) {  // near the wall at 0 (normal +e_k)
+    const float xabs = (float)bc[k] + xp[k];
+    if (xabs < rpf + mrg) {  // near the wall at 0 (normal +e_k)
       const double delta = A.rad[p] - A.X[k * np + p];
       if (delta > 0.0) Fc[k] += A.ph.kn * delta - A.gw[p] * A.U[k * np + p];
     }
-    if (xp[k] > nk - rpf - mrg) {  // near the wall at n (normal -e_k)
+    if (xabs > nk - rpf - mrg) {  // near the wall at n (normal -e_k)
       const double delta = A.rad[p] - ((double)g.n[k] - A.X[k * np + p]);
       if (delta > 0.0) Fc[k] -= A.ph.kn * delta + A.gw[p] * A.U[k * np + p];
     }
@@ -522,8 +602,12 @@ __global__ void __launch_bounds__(256) k_couple(CoupleArgs A) {
   FT amp[3] = {FT(0), FT(0), FT(0)};
   bool act = sl < A.np;
   unsigned p = 0;
+  int4 mc = make_int4(0, 0, 0, 0);
+  float4 mf = make_float4(0.f, 0.f, 0.f, 0.f);
   if (act) {
-    p = A.perm[sl];
+    mc = A.cs[sl];
+    mf = A.xs[sl];
+    p = (unsigned)mc.w;
     if (p >= (unsigned)np) {
       atomicOr(A.err, ERR_INDEX);
       act = false;
@@ -541,9 +625,15 @@ __global__ void __launch_bounds__(256) k_couple(CoupleArgs A) {
     const R* mom = (const R*)A.mom;
 
     // --- interpolation of rho, j (Eq. 4) ---
-    axis_taps<W, R>(X[0], g.n[0], g.periodic[0], tx);
-    axis_taps<W, R>(X[1], g.n[1], g.periodic[1], ty);
-    if constexpr (D == 3) axis_taps<W, R>(X[2], g.n[2], g.periodic[2], tz);
+    if constexpr (sizeof(R) == 4) {
+      axis_taps_local<W>(mc.x, mf.x, g.n[0], g.periodic[0], tx);
+      axis_taps_local<W>(mc.y, mf.y, g.n[1], g.periodic[1], ty);
+      if constexpr (D == 3) axis_taps_local<W>(mc.z, mf.z, g.n[2], g.periodic[2], tz);
+    } else {
+      axis_taps<W, R>(X[0], g.n[0], g.periodic[0], tx);
+      axis_taps<W, R>(X[1], g.n[1], g.periodic[1], ty);
+      if constexpr (D == 3) axis_taps<W, R>(X[2], g.n[2], g.periodic[2], tz);
+    }
     R rs = R(0), js[3] = {R(0), R(0), R(0)};
 #pragma unroll 1
     for (int iz = 0; iz < WZ; ++iz) {
@@ -580,7 +670,7 @@ __global__ void __launch_bounds__(256) k_couple(CoupleArgs A) {
     // --- particle update (Eq. 13) and force density (Eqs. 6-7) ---
     double Un[3], Ub[3], gg[3];
     if (A.ph.implicit_drag) {
-      const double inv = 1.0 / (mi + 2.0 * Ap * rho_l);
+      const double inv = rcp_newton<sizeof(R) == 4 ? 1 : 2>(mi + 2.0 * Ap * rho_l);
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         Un[k] = (mi * U[k] + 2.0 * Ap * j_l[k] + bu * A.ph.gravity[k] + Fc[k]) * inv;
@@ -598,7 +688,8 @@ __global__ void __launch_bounds__(256) k_couple(CoupleArgs A) {
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       gg[k] = 2.0 * (rho_l * Ub[k] - j_l[k]);
-      amp[k] = (FT)(Ap * gg[k]);
+      if constexpr (sizeof(FT) == 4) amp[k] = (float)gg[k] * (float)Ap;
+      else amp[k] = (FT)(Ap * gg[k]);
       double xn = X[k] + Un[k];
       if (g.periodic[k]) {
         const double N = (double)g.n[k];
@@ -606,10 +697,10 @@ __global__ void __launch_bounds__(256) k_couple(CoupleArgs A) {
         else if (xn >= N) xn -= N;
         if (!(xn >= 0.0 && xn < N)) xn = xn - N * floor(xn / N);  // |U| > N: not physical
         if (!(xn >= 0.0 && xn < N)) xn = 0.0;
-      } else if (xn < 0.0 || xn > (double)g.n[k]) {
+      } else if (outside_bits(xn, (double)g.n[k])) {
         esc = true;
       }
-      bad |= !isfinite(xn) || !isfinite(Un[k]);
+      bad |= not_finite_bits(xn) || not_finite_bits(Un[k]);
       A.Xn[k * np + p] = xn;
       A.Un[k * np + p] = Un[k];
       A.gout[k * np + p] = gg[k];
@@ -788,21 +879,21 @@ cudaError_t launch_bin(const State& s, cudaStream_t st, int* nk) {
   const double* X = P.X[s.cur];
   if (s.geo.d == 2)
     k_bin_key<2><<<blocks_for(P.np, 256), 256, 0, st>>>(X, P.np, s.geo, P.bm, P.radf, P.key,
-                                                        P.rank, P.bin_cnt, P.xr);
+                                                        P.rank, P.bin_cnt, P.xr, P.cr);
   else
     k_bin_key<3><<<blocks_for(P.np, 256), 256, 0, st>>>(X, P.np, s.geo, P.bm, P.radf, P.key,
-                                                        P.rank, P.bin_cnt, P.xr);
+                                                        P.rank, P.bin_cnt, P.xr, P.cr);
   const long long n = P.nbin + 1;
   k_scan_reduce<<<P.scan_blocks, SCAN_THREADS, 0, st>>>(P.bin_cnt, n, P.block_sums);
   k_scan_top<<<1, SCAN_THREADS, 0, st>>>(P.block_sums, P.scan_blocks);
   k_scan_down<<<P.scan_blocks, SCAN_THREADS, 0, st>>>(P.bin_cnt, n, P.block_sums);
   k_bin_scatter<<<blocks_for(P.np, 256), 256, 0, st>>>(P.key, P.rank, P.bin_cnt, P.np, P.xr,
-                                                       P.perm, P.xs);
+                                                       P.cr, P.perm, P.xs, P.cs);
   if (nk) *nk += 5;
   if (s.deterministic) {
     // bins in particle-id order: every sum over a bin then runs in a fixed order
     k_bin_sort<<<blocks_for(P.np, 256), 256, 0, st>>>(P.key, P.rank, P.bin_cnt, P.np, P.xr,
-                                                      P.perm, P.xs);
+                                                      P.cr, P.perm, P.xs, P.cs);
     if (nk) *nk += 1;
   }
   return cudaGetLastError();
@@ -827,12 +918,9 @@ CoupleArgs couple_args(const State& s) {
   A.gw = P.gw;
   A.radf = P.radf;
   A.xs = P.xs;
-  {
-    // positions below 2^e round to FP32 within 2^(e-24) per coordinate
-    int mx = s.geo.n[0] > s.geo.n[1] ? s.geo.n[0] : s.geo.n[1];
-    mx = mx > s.geo.n[2] ? mx : s.geo.n[2];
-    A.xf_margin = 8.0f * (float)mx * 5.9604645e-8f + 1e-6f;
-  }
+  A.cs = P.cs;
+  // in-cell offsets are exact to 2^-24 and whole-cell differences exactly so
+  A.xf_margin = 1e-5f;
   A.gout = P.g;
   A.Fcout = P.Fc;
   A.perm = P.perm;

@@ -219,8 +219,10 @@ struct Particles {
   double* buoy;   // mass * (1 - 1 / rho_r)
   double* gw;     // wall damping coefficient 2 beta sqrt(mass kn)
   float* radf;    // radius in FP32 (contact pre-filter)
-  float4* xr;     // [np] FP32 position and radius by particle id (written by binning)
-  float4* xs;     // [np] the same in sorted order (contact pre-filter)
+  float4* xr;     // [np] FP32 in-cell position and radius by particle id (binning)
+  int4* cr;       // [np] cell (x, y, z) and particle id, by particle id (binning)
+  float4* xs;     // [np] xr in sorted (slot) order
+  int4* cs;       // [np] cr in sorted (slot) order
   double* g;      // [d][np] force density of the last step (Eq. 7)
   double* Fc;     // [d][np] contact force of the last step
   // cell list (bins = lattice cells)
