@@ -76,6 +76,8 @@ extern "C" {
  * particle integration are FP64 in every mode */
 #define PIBM_FP64 0 /* populations, collision and spread force in FP64 */
 #define PIBM_FP32 1 /* populations stored as f - w in FP32, FP32 collision and force field */
+#define PIBM_FP16 2 /* populations stored as (f - w) * 2^12 in FP16, FP32 collision and force */
+#define PIBM_BF16 3 /* populations stored as f - w in BF16, FP32 collision and force field */
 
 /* fields for pibm_read_fields (bit k selects dst[k]) */
 #define PIBM_FIELD_RHO (1u << 0) /* ncell: rho = sum_a f_a of the current state */
@@ -96,7 +98,7 @@ typedef struct pibm_config {
   double gravity[3];   /* acceleration on the particles; the fluid carries none */
   int delta_width;     /* 2 (linear hat) or 4 (cosine kernel, Eq. 11) */
   int coupling;        /* PIBM_IMPLICIT or PIBM_EXPLICIT */
-  int precision;       /* PIBM_FP64 or PIBM_FP32 */
+  int precision;       /* PIBM_FP64, PIBM_FP32, PIBM_FP16 or PIBM_BF16 */
   int deterministic;   /* 0: spread with atomics; 1: ordered per-cell gather,
                           bitwise reproducible run to run */
   double dem_kn;       /* contact stiffness */

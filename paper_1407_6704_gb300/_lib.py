@@ -23,7 +23,7 @@ PIBM_ETOOBIG = -8
 PIBM_D2Q9, PIBM_D3Q15, PIBM_D3Q19 = 9, 15, 19
 PIBM_WALL, PIBM_PERIODIC = 0, 1
 PIBM_IMPLICIT, PIBM_EXPLICIT = 0, 1
-PIBM_FP64, PIBM_FP32 = 0, 1
+PIBM_FP64, PIBM_FP32, PIBM_FP16, PIBM_BF16 = 0, 1, 2, 3
 
 FIELD_RHO, FIELD_J, FIELD_POP, FIELD_X, FIELD_U = (1 << k for k in range(5))
 NFIELDS = 5

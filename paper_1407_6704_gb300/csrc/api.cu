@@ -42,6 +42,10 @@ struct Layout {
 
 int dims_of(int lattice) { return lattice == PIBM_D2Q9 ? 2 : 3; }
 
+size_t pop_bytes(int precision) {
+  return precision == PIBM_FP64 ? 8 : (precision == PIBM_FP32 ? 4 : 2);
+}
+
 // Tile shape of the particle kernel: 32 x 8 cells in 2D, 16 x 8 x 4 in 3D.
 BinMap bin_map(const pibm_config* c) {
   BinMap b;
@@ -78,7 +82,9 @@ int validate(const pibm_config* c) {
   if (!(c->tau > 0.5) || !isfinite(c->tau)) return PIBM_EINVAL;
   if (c->delta_width != 2 && c->delta_width != 4) return PIBM_EINVAL;
   if (c->coupling != PIBM_IMPLICIT && c->coupling != PIBM_EXPLICIT) return PIBM_EINVAL;
-  if (c->precision != PIBM_FP64 && c->precision != PIBM_FP32) return PIBM_EINVAL;
+  if (c->precision != PIBM_FP64 && c->precision != PIBM_FP32 && c->precision != PIBM_FP16 &&
+      c->precision != PIBM_BF16)
+    return PIBM_EINVAL;
   if (!(c->dem_kn >= 0.0) || !isfinite(c->dem_kn)) return PIBM_EINVAL;
   if (!(c->dem_restitution > 0.0 && c->dem_restitution <= 1.0)) return PIBM_EINVAL;
   for (int k = 0; k < 3; ++k)
@@ -112,7 +118,8 @@ Layout layout(const pibm_config* c) {
   const int q = c->lattice, d = dims_of(q);
   const long long ncell = c->n[0] * c->n[1] * c->n[2];
   const long long pitch = (ncell + 63) / 64 * 64;
-  const size_t ts = c->precision == PIBM_FP64 ? 8 : 4;
+  const size_t ts = pop_bytes(c->precision);           // population element
+  const size_t fs = c->precision == PIBM_FP64 ? 8 : 4;  // force and moment element
   const long long np = c->n_particles;
   const long long nbin = bin_count(c);
   const long long scan_blocks = (nbin + 1 + 8191) / 8192;
@@ -123,8 +130,8 @@ Layout layout(const pibm_config* c) {
     return o;
   };
   L.f = take(2 * align_up((size_t)q * pitch * ts));
-  L.F = take((size_t)(d == 2 ? 2 : 4) * pitch * ts);
-  L.mom = take(c->n_particles > 0 ? (size_t)MOM_SLOTS * pitch * ts : 0);
+  L.F = take((size_t)(d == 2 ? 2 : 4) * pitch * fs);
+  L.mom = take(c->n_particles > 0 ? (size_t)MOM_SLOTS * pitch * fs : 0);
   L.red = take(sizeof(double) * RED_SCRATCH);
   L.err = take(sizeof(unsigned));
   L.out = take(sizeof(double) * 8);
@@ -333,7 +340,8 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
   s.phy.implicit_drag = cfg->coupling == PIBM_IMPLICIT;
   s.precision = cfg->precision;
   s.deterministic = cfg->deterministic ? 1 : 0;
-  const size_t ts = cfg->precision == PIBM_FP64 ? 8 : 4;
+  const size_t ts = pop_bytes(cfg->precision);
+  const size_t fs = cfg->precision == PIBM_FP64 ? 8 : 4;
   const size_t fbuf = align_up((size_t)q * s.geo.pitch * ts);
   s.f[0] = base + L.f;
   s.f[1] = base + L.f + fbuf;
@@ -378,7 +386,7 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
     return code;
   };
   // force field and health word start at zero
-  if (cudaMemsetAsync(s.F, 0, (size_t)(d == 2 ? 2 : 4) * s.geo.pitch * ts, st) != cudaSuccess ||
+  if (cudaMemsetAsync(s.F, 0, (size_t)(d == 2 ? 2 : 4) * s.geo.pitch * fs, st) != cudaSuccess ||
       cudaMemsetAsync(s.err, 0, sizeof(unsigned), st) != cudaSuccess)
     return fail(PIBM_ECUDA);
 
@@ -485,7 +493,7 @@ int pibm_forces(pibm_t* h, double* f_fpi, double* f_contact, int on_device) {
       double* a = stage;
       double* b = stage + (size_t)d * np;
       size_t need = sizeof(double) * 2 * d * np;
-      size_t have = align_up((size_t)s.geo.q * s.geo.pitch * (s.precision == PIBM_FP64 ? 8 : 4));
+      size_t have = align_up((size_t)s.geo.q * s.geo.pitch * pop_bytes(s.precision));
       if (need > have) return PIBM_ENOMEM;
       CK(launch_particle_forces(s, f_fpi ? a : nullptr, f_contact ? b : nullptr, h->stream));
       if (f_fpi)

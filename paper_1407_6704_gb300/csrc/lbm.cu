@@ -52,47 +52,17 @@ __device__ __forceinline__ bool bad_density(float r) {
 __device__ __forceinline__ bool nonzero_bits(double v) { return __double_as_longlong(v) != 0; }
 __device__ __forceinline__ bool nonzero_bits(float v) { return __float_as_uint(v) != 0u; }
 
-// Pull-stream, collide, store. FT: type of the force field.
-template <int Q, class St, typename FT>
-__global__ void __launch_bounds__(256) k_collide_stream(const typename St::T* __restrict__ fin,
-                                                        typename St::T* __restrict__ fout,
-                                                        FT* __restrict__ F, Geometry g,
-                                                        typename St::R om,
-                                                        typename St::R cF,
-                                                        unsigned* __restrict__ err) {
+// Guo-forced BGK collision of one cell (Eqs. 2, 3, 8), on stored values s
+// (s = f - S w) and the force Fv of this step; writes the post-collision stored
+// values to out.
+template <int Q, class St>
+__device__ __forceinline__ void collide_cell(const typename St::R (&s)[Q],
+                                             const typename St::R (&Fv)[3], typename St::R om,
+                                             typename St::R cF, unsigned* __restrict__ err,
+                                             typename St::R (&out)[Q]) {
   using L = Lattice<Q>;
-  using T = typename St::T;
   using R = typename St::R;
   constexpr int D = L::D;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
-  if (x >= g.n[0] || y >= g.n[1]) return;
-  const long long c = x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
-  const long long P = g.pitch;
-
-  R s[Q];
-#pragma unroll
-  for (int a = 0; a < Q; ++a) {
-    bool bb;
-    long long src = pull_src<Q>(g, x, y, z, a, bb);
-    s[a] = (R)(bb ? fin[opp(a) * P + c] : fin[a * P + src]);
-  }
-
-  // force of this step, consumed here and cleared for the next spread
-  R Fv[3] = {R(0), R(0), R(0)};
-  {
-    FT v[3];
-    load_force<D, FT>(F, c, v);
-    bool any = false;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      any |= nonzero_bits(v[k]);
-      Fv[k] = (R)v[k];
-    }
-    if (any) clear_force<D, FT>(F, c);
-  }
-
   // moments: sum of stored values and first moment
   R sum = R(0), j[3] = {R(0), R(0), R(0)};
 #pragma unroll
@@ -130,7 +100,7 @@ __global__ void __launch_bounds__(256) k_collide_stream(const typename St::T* __
   const R K = R(9) * cF;
   const R Dd = R(3) * om * rho;
   const R E3 = R(3) * cF;
-  fout[c] = (T)(om1 * s[0] + R(L::w(0)) * G);
+  out[0] = om1 * s[0] + R(L::w(0)) * G;
 #pragma unroll
   for (int a = 1; a < Q; a += 2) {
     const R w = R(L::w(a));
@@ -147,8 +117,167 @@ __global__ void __launch_bounds__(256) k_collide_stream(const typename St::T* __
     }
     const R Ev = w * (G + eu * (H * eu + K * eF));
     const R Od = w * (Dd * eu + E3 * eF);
-    fout[a * P + c] = (T)(om1 * s[a] + (Ev + Od));
-    fout[(a + 1) * P + c] = (T)(om1 * s[a + 1] + (Ev - Od));
+    out[a] = om1 * s[a] + (Ev + Od);
+    out[a + 1] = om1 * s[a + 1] + (Ev - Od);
+  }
+}
+
+// Force of this step at cell c, consumed and cleared for the next spread.
+template <int D, typename FT, typename R>
+__device__ __forceinline__ void take_force(FT* __restrict__ F, long long c, R (&Fv)[3]) {
+  FT v[3];
+  load_force<D, FT>(F, c, v);
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) Fv[k] = R(0);
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    any |= nonzero_bits(v[k]);
+    Fv[k] = (R)v[k];
+  }
+  if (any) clear_force<D, FT>(F, c);
+}
+
+// Pull-stream, collide, store; one thread per cell. FT: type of the force field.
+template <int Q, class St, typename FT>
+__global__ void __launch_bounds__(256) k_collide_stream(const typename St::T* __restrict__ fin,
+                                                        typename St::T* __restrict__ fout,
+                                                        FT* __restrict__ F, Geometry g,
+                                                        typename St::R om,
+                                                        typename St::R cF,
+                                                        unsigned* __restrict__ err) {
+  using L = Lattice<Q>;
+  using R = typename St::R;
+  constexpr int D = L::D;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= g.n[0] || y >= g.n[1]) return;
+  const long long c = x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
+  const long long P = g.pitch;
+
+  R s[Q];
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    bool bb;
+    long long src = pull_src<Q>(g, x, y, z, a, bb);
+    s[a] = St::load(bb ? fin[opp(a) * P + c] : fin[a * P + src]);
+  }
+  R Fv[3];
+  take_force<D, FT, R>(F, c, Fv);
+  R out[Q];
+  collide_cell<Q, St>(s, Fv, om, cF, err, out);
+#pragma unroll
+  for (int a = 0; a < Q; ++a) fout[a * P + c] = St::store(out[a]);
+}
+
+// The same for 16-bit storage, two neighbouring cells (x0, x0 + 1) per thread
+// and one warp per 64 cells of a row: every population row is read with aligned
+// 32-bit pair loads; the value one cell to the left or right comes from the
+// neighbouring lane (warp shuffle), and only the warp's edge lanes and the
+// domain edges load a single extra element. Requires an even n[0].
+template <int Q, class St, typename FT>
+__global__ void __launch_bounds__(256) k_collide_stream_pair(const typename St::T* __restrict__ fin,
+                                                             typename St::T* __restrict__ fout,
+                                                             FT* __restrict__ F, Geometry g,
+                                                             typename St::R om,
+                                                             typename St::R cF,
+                                                             unsigned* __restrict__ err) {
+  using L = Lattice<Q>;
+  using R = typename St::R;
+  constexpr int D = L::D;
+  static_assert(sizeof(typename St::T) == 2, "pair kernel is for 16-bit storage");
+  const int lane = threadIdx.x;  // blockDim.x == 32
+  const int x0 = 2 * (blockIdx.x * 32 + lane);
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (y >= g.n[1]) return;  // whole warp (one row per warp)
+  const int n0 = g.n[0];
+  const bool act = x0 < n0;
+  const long long P = g.pitch;
+  const long long c0 = x0 + (long long)n0 * (y + (long long)g.n[1] * z);
+  const unsigned short* fb = reinterpret_cast<const unsigned short*>(fin);
+  auto pair_at = [&](long long idx) -> unsigned {  // idx even
+    return *reinterpret_cast<const unsigned*>(fb + idx);
+  };
+
+  // source row of every population: wraps on periodic axes, bounces at walls
+  // (then the whole row bounces); three passes keep every load in flight at once
+  long long rowb[Q];
+  bool rowbb[Q];
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    int ys = y - L::e(a, 1), zs = z - L::e(a, 2);
+    bool bb = false;
+    if (L::e(a, 1) != 0 && (ys < 0 || ys >= g.n[1])) {
+      if (g.periodic[1]) ys = ys < 0 ? ys + g.n[1] : ys - g.n[1];
+      else bb = true;
+    }
+    if (L::e(a, 2) != 0 && (zs < 0 || zs >= g.n[2])) {
+      if (g.periodic[2]) zs = zs < 0 ? zs + g.n[2] : zs - g.n[2];
+      else bb = true;
+    }
+    rowbb[a] = bb;
+    rowb[a] = (long long)n0 * (ys + (long long)g.n[1] * zs);
+  }
+  // pass 1: one aligned pair per population
+  unsigned mine[Q];
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    const long long pa = (long long)a * P, po = (long long)opp(a) * P;
+    mine[a] = 0u;
+    if (act) mine[a] = rowbb[a] ? pair_at(po + c0) : pair_at(pa + rowb[a] + x0);
+  }
+  // pass 2: the single elements the warp's edge lanes and the domain edges need
+  unsigned short fix[Q];
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    const int ex = L::e(a, 0);
+    const long long pa = (long long)a * P, po = (long long)opp(a) * P;
+    fix[a] = 0;
+    if (ex == 0 || rowbb[a] || !act) continue;
+    if (ex > 0 && (lane == 0 || x0 == 0)) {  // needs x0 - 1
+      if (x0 == 0) fix[a] = g.periodic[0] ? fb[pa + rowb[a] + (n0 - 1)] : fb[po + c0];
+      else fix[a] = fb[pa + rowb[a] + x0 - 1];
+    } else if (ex < 0 && (lane == 31 || x0 + 2 >= n0)) {  // needs x0 + 2
+      if (x0 + 2 >= n0) fix[a] = g.periodic[0] ? fb[pa + rowb[a]] : fb[po + c0 + 1];
+      else fix[a] = fb[pa + rowb[a] + x0 + 2];
+    }
+  }
+  // pass 3: neighbours through the warp, then the values of the two cells
+  R s[2][Q];
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    const int ex = L::e(a, 0);
+    unsigned short v0 = (unsigned short)(mine[a] & 0xffffu), v1 = (unsigned short)(mine[a] >> 16);
+    if (ex > 0) {  // sources x0 - 1, x0 (rowbb is warp-uniform: one row per warp)
+      const unsigned left = __shfl_up_sync(0xffffffffu, mine[a], 1);
+      if (!rowbb[a]) {
+        v1 = v0;
+        v0 = (lane == 0 || x0 == 0) ? fix[a] : (unsigned short)(left >> 16);
+      }
+    } else if (ex < 0) {  // sources x0 + 1, x0 + 2
+      const unsigned right = __shfl_down_sync(0xffffffffu, mine[a], 1);
+      if (!rowbb[a]) {
+        v0 = v1;
+        v1 = (lane == 31 || x0 + 2 >= n0) ? fix[a] : (unsigned short)(right & 0xffffu);
+      }
+    }
+    s[0][a] = St::load_bits(v0);
+    s[1][a] = St::load_bits(v1);
+  }
+  if (!act) return;
+  R Fv0[3], Fv1[3];
+  take_force<D, FT, R>(F, c0, Fv0);
+  take_force<D, FT, R>(F, c0 + 1, Fv1);
+  R o0[Q], o1[Q];
+  collide_cell<Q, St>(s[0], Fv0, om, cF, err, o0);
+  collide_cell<Q, St>(s[1], Fv1, om, cF, err, o1);
+  unsigned short* ob = reinterpret_cast<unsigned short*>(fout);
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    const unsigned pr = (unsigned)St::store_bits(o0[a]) | ((unsigned)St::store_bits(o1[a]) << 16);
+    *reinterpret_cast<unsigned*>(ob + (long long)a * P + c0) = pr;
   }
 }
 
@@ -164,7 +293,7 @@ __global__ void k_store_plane(typename St::T* __restrict__ f, const double* __re
   for (int b = 0; b < Q; ++b)
     if (b == a) wa = Lattice<Q>::w(b);
   double shift = St::S ? wa : 0.0;
-  f[c] = (typename St::T)((src ? src[c] : wa) - shift);
+  f[c] = St::store((typename St::R)((src ? src[c] : wa) - shift));
 }
 
 // Post-stream population a of the current state, FP64.
@@ -183,7 +312,7 @@ __global__ void k_read_pop(const typename St::T* __restrict__ fin, double* __res
     if (b != a) continue;
     bool bb;
     long long src = pull_src<Q>(g, x, y, z, b, bb);
-    v = (double)(bb ? fin[opp(b) * g.pitch + c] : fin[b * g.pitch + src]);
+    v = (double)St::load(bb ? fin[opp(b) * g.pitch + c] : fin[b * g.pitch + src]);
     v += St::S ? Lattice<Q>::w(b) : 0.0;
   }
   dst[c] = v;
@@ -204,7 +333,7 @@ __global__ void k_read_moment(const typename St::T* __restrict__ fin, double* __
   for (int b = 0; b < Q; ++b) {
     bool bb;
     long long src = pull_src<Q>(g, x, y, z, b, bb);
-    double v = (double)(bb ? fin[opp(b) * g.pitch + c] : fin[b * g.pitch + src]);
+    double v = (double)St::load(bb ? fin[opp(b) * g.pitch + c] : fin[b * g.pitch + src]);
     r += v;
     if (comp > 0) m += L::e(b, comp - 1) * v;
   }
@@ -255,7 +384,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_fluid_sums(const typename St::T
     for (int b = 0; b < Q; ++b) {
       bool bb;
       long long src = pull_src<Q>(g, x, y, z, b, bb);
-      double v = (double)(bb ? fin[opp(b) * g.pitch + c] : fin[b * g.pitch + src]);
+      double v = (double)St::load(bb ? fin[opp(b) * g.pitch + c] : fin[b * g.pitch + src]);
       r += v;
 #pragma unroll
       for (int k = 0; k < D; ++k)
@@ -299,10 +428,20 @@ dim3 cell_block(const Geometry& g) {
 template <int Q, class St, typename FT>
 cudaError_t collide_stream_t(const State& s, cudaStream_t st) {
   const Geometry& g = s.geo;
-  dim3 blk = cell_block(g);
-  dim3 grd((g.n[0] + blk.x - 1) / blk.x, (g.n[1] + blk.y - 1) / blk.y, g.n[2]);
   using T = typename St::T;
   using R = typename St::R;
+  if constexpr (sizeof(T) == 2) {
+    if ((g.n[0] & 1) == 0) {
+      dim3 blk(32, 8, 1);
+      dim3 grd((g.n[0] + 63) / 64, (g.n[1] + blk.y - 1) / blk.y, g.n[2]);
+      k_collide_stream_pair<Q, St, FT><<<grd, blk, 0, st>>>(
+          (const T*)s.f[s.cur], (T*)s.f[1 - s.cur], (FT*)s.F, g, (R)s.phy.omega, (R)s.phy.cF,
+          s.err);
+      return cudaGetLastError();
+    }
+  }
+  dim3 blk = cell_block(g);
+  dim3 grd((g.n[0] + blk.x - 1) / blk.x, (g.n[1] + blk.y - 1) / blk.y, g.n[2]);
   k_collide_stream<Q, St, FT><<<grd, blk, 0, st>>>((const T*)s.f[s.cur], (T*)s.f[1 - s.cur],
                                                    (FT*)s.F, g, (R)s.phy.omega, (R)s.phy.cF,
                                                    s.err);
@@ -320,6 +459,14 @@ cudaError_t dispatch(const State& s, Fn fn) {
     if (s.geo.q == 9) return fn(Lattice<9>{}, StoreF32{}, float{});
     if (s.geo.q == 15) return fn(Lattice<15>{}, StoreF32{}, float{});
     if (s.geo.q == 19) return fn(Lattice<19>{}, StoreF32{}, float{});
+  } else if (s.precision == PIBM_FP16) {
+    if (s.geo.q == 9) return fn(Lattice<9>{}, StoreF16{}, float{});
+    if (s.geo.q == 15) return fn(Lattice<15>{}, StoreF16{}, float{});
+    if (s.geo.q == 19) return fn(Lattice<19>{}, StoreF16{}, float{});
+  } else if (s.precision == PIBM_BF16) {
+    if (s.geo.q == 9) return fn(Lattice<9>{}, StoreBF16{}, float{});
+    if (s.geo.q == 15) return fn(Lattice<15>{}, StoreBF16{}, float{});
+    if (s.geo.q == 19) return fn(Lattice<19>{}, StoreBF16{}, float{});
   }
   return cudaErrorInvalidValue;
 }

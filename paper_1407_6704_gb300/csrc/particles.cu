@@ -361,7 +361,7 @@ __device__ __forceinline__ void pull_moments(const typename St::T* __restrict__ 
       else if (s2 >= g.n[2]) { if (g.periodic[2]) s2 -= g.n[2]; else bb = true; }
     }
     long long src = s0 + (long long)g.n[0] * (s1 + (long long)g.n[1] * s2);
-    R v = (R)(bb ? f[opp(a) * g.pitch + c] : f[a * g.pitch + src]);
+    R v = St::load(bb ? f[opp(a) * g.pitch + c] : f[a * g.pitch + src]);
     s += v;
     if (L::e(a, 0)) m0 += L::e(a, 0) * v;
     if (L::e(a, 1)) m1 += L::e(a, 1) * v;
@@ -981,10 +981,18 @@ cudaError_t launch_couple(const State& s, cudaStream_t st, int* nk) {
     if (q == 9) return couple_w<9, StoreF64, double>(s, st, nk);
     if (q == 15) return couple_w<15, StoreF64, double>(s, st, nk);
     if (q == 19) return couple_w<19, StoreF64, double>(s, st, nk);
-  } else {
+  } else if (s.precision == PIBM_FP32) {
     if (q == 9) return couple_w<9, StoreF32, float>(s, st, nk);
     if (q == 15) return couple_w<15, StoreF32, float>(s, st, nk);
     if (q == 19) return couple_w<19, StoreF32, float>(s, st, nk);
+  } else if (s.precision == PIBM_FP16) {
+    if (q == 9) return couple_w<9, StoreF16, float>(s, st, nk);
+    if (q == 15) return couple_w<15, StoreF16, float>(s, st, nk);
+    if (q == 19) return couple_w<19, StoreF16, float>(s, st, nk);
+  } else if (s.precision == PIBM_BF16) {
+    if (q == 9) return couple_w<9, StoreBF16, float>(s, st, nk);
+    if (q == 15) return couple_w<15, StoreBF16, float>(s, st, nk);
+    if (q == 19) return couple_w<19, StoreBF16, float>(s, st, nk);
   }
   return cudaErrorInvalidValue;
 }

@@ -3,6 +3,8 @@
 // each translation unit provides.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -63,17 +65,49 @@ __host__ __device__ constexpr int opp(int a) { return a == 0 ? 0 : ((a & 1) ? a 
 
 // ---------------------------------------------------------------------------
 // Population storage. The stored value is s = f - S w_a (S = 1: shifted),
-// held in type T and operated on in type R.
+// held in type T (possibly scaled) and operated on in type R.
 // ---------------------------------------------------------------------------
+// load() turns a stored value into s (type R), store() the reverse.
 struct StoreF64 {
   using T = double;
   using R = double;
   static constexpr int S = 0;
+  __device__ static __forceinline__ R load(T v) { return v; }
+  __device__ static __forceinline__ T store(R v) { return v; }
 };
 struct StoreF32 {
   using T = float;
   using R = float;
   static constexpr int S = 1;
+  __device__ static __forceinline__ R load(T v) { return v; }
+  __device__ static __forceinline__ T store(R v) { return v; }
+};
+// Half precision keeps f - w scaled by 2^12, so that deviations of 1e-7 .. 1e1
+// stay in FP16's normal range (6.1e-5 .. 65504 after scaling).
+struct StoreF16 {
+  using T = __half;
+  using R = float;
+  static constexpr int S = 1;
+  __device__ static __forceinline__ R load(T v) { return __half2float(v) * 2.44140625e-4f; }
+  __device__ static __forceinline__ T store(R v) { return __float2half_rn(v * 4096.f); }
+  __device__ static __forceinline__ R load_bits(unsigned short b) { return load(__ushort_as_half(b)); }
+  __device__ static __forceinline__ unsigned short store_bits(R v) {
+    return __half_as_ushort(store(v));
+  }
+};
+// BF16 has FP32's exponent range, so f - w is stored unscaled.
+struct StoreBF16 {
+  using T = __nv_bfloat16;
+  using R = float;
+  static constexpr int S = 1;
+  __device__ static __forceinline__ R load(T v) { return __bfloat162float(v); }
+  __device__ static __forceinline__ T store(R v) { return __float2bfloat16_rn(v); }
+  __device__ static __forceinline__ R load_bits(unsigned short b) {
+    return load(__ushort_as_bfloat16(b));
+  }
+  __device__ static __forceinline__ unsigned short store_bits(R v) {
+    return __bfloat16_as_ushort(store(v));
+  }
 };
 
 // Force and moment fields are cell-major: FSTRIDE force slots per cell (2 in 2D,

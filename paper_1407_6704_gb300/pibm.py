@@ -12,7 +12,8 @@ from . import _lib
 from ._lib import (FIELD_J, FIELD_POP, FIELD_RHO, FIELD_U, FIELD_X, PibmConfig, check)
 
 _LATTICES = {"d2q9": 9, "d3q15": 15, "d3q19": 19, 9: 9, 15: 15, 19: 19}
-_PRECISION = {"fp64": _lib.PIBM_FP64, "fp32": _lib.PIBM_FP32}
+_PRECISION = {"fp64": _lib.PIBM_FP64, "fp32": _lib.PIBM_FP32, "fp16": _lib.PIBM_FP16,
+              "bf16": _lib.PIBM_BF16}
 
 
 def _dptr(a):
@@ -34,7 +35,7 @@ class Pibm:
     lattice: "d2q9" | "d3q15" | "d3q19"; n: extents (2 or 3 ints);
     periodic: per-axis flags (False = walls at 0 and n); tau: BGK relaxation time;
     gravity: particle acceleration; delta_width: 2 or 4; implicit: drag coupling;
-    precision: "fp64" | "fp32"; deterministic: ordered spreading;
+    precision: "fp64" | "fp32" | "fp16" | "bf16"; deterministic: ordered spreading;
     x0, u0 (n_particles, d), diameter, density_ratio (n_particles,);
     f0: optional (q, ...) post-stream populations of step 0.
     """
