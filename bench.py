@@ -316,11 +316,59 @@ def run_gpu(args, rank, world):
             line[p]["collide_roofline"] = {"bound": "alu", "achieved": a,
                                            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                                            "frac": a / FP64_PEAK_TFLOPS}
+    if args.ensemble:
+        line["ensemble"] = ensemble_bench(args)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, w)
     if dist is not None:
         dist.destroy_process_group()
     return line
+
+
+def ensemble_bench(args, k=None):
+    """The batched ensemble (64 independent 2D instances, 64^2..512^2, FP32):
+    K steps through one graph launch per two steps for all members, against the
+    same members stepped one after another (each through its own graphs), after
+    each member's stream-collide block shape is autotuned."""
+    import torch
+    from paper_1407_6704_gb300.inputs import ensemble_workloads
+    from paper_1407_6704_gb300.pibm import Ensemble, Pibm
+
+    ws = ensemble_workloads()
+    k = k or min(args.steps, 400)
+    cells = sum(w.ncell for w, _ in ws)
+    sims = [Pibm.from_workload(w, precision="fp32", particles=p) for w, p in ws]
+    for s in sims:
+        s.autotune()
+        s.step(args.warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for s in sims:
+        s.step(k)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1) / k
+    ens = Ensemble(sims)
+    ens.step(args.warmup + (args.warmup % 2))
+    ens.status()
+    e0.record(ens.stream)
+    ens.step(k)
+    e1.record(ens.stream)
+    torch.cuda.synchronize()
+    ms_ens = e0.elapsed_time(e1) / k
+    status = ens.status()
+    ens.close()
+    for s in sims:
+        s.close()
+    return {"workload": "64 independent 2D D2Q9 sedimentation instances, sides 64..512 "
+                        "log-uniform, 100..20k particles, tau 0.55..1.0, ratio 1.5..3.0, "
+                        "d 0.5, 2-point delta, FP32",
+            "cells": cells, "particles": sum(w.n_particles for w, _ in ws), "steps": k,
+            "ms_per_step": ms_ens, "value": cells / (ms_ens * 1e-3) / 1e6, "unit": "MLUPS",
+            "members_one_by_one_ms_per_step": ms_seq,
+            "members_one_by_one_value": cells / (ms_seq * 1e-3) / 1e6, "status": status}
 
 
 def cpu_sample(w, side=256):
@@ -414,6 +462,7 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "fp64", "fp16", "bf16"], default="fp32")
     ap.add_argument("--both", type=int, default=1, help="also time the other precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ensemble", type=int, default=1, help="also time the 64-member ensemble")
     ap.add_argument("--profile-only", action="store_true",
                     help="only run --steps phase-by-phase steps (ncu driver); prints phase times")
     args = ap.parse_args()

@@ -166,6 +166,29 @@ int pibm_kernels_per_step(pibm_t* h);
  * last). Synchronises the stream. Not part of the method; a timing aid. */
 int pibm_profile_steps(pibm_t* h, int64_t nsteps, double* phase_ms);
 
+/* Pick the block shape of the fused stream-collide kernel for this handle by
+ * timing a fixed list of candidates on its stream (not part of the method; a
+ * tuning aid). The timing runs leave the simulation state unchanged. block_xy
+ * (may be NULL) receives the chosen shape. Synchronises the stream. */
+int pibm_autotune(pibm_t* h, int* block_xy);
+
+/* Ensembles: independent simulations (each made by pibm_create, possibly with
+ * different lattices, particle counts and parameters) that advance together.
+ * pibm_ensemble_step captures two steps of every member into one CUDA graph,
+ * one independent branch per member, and replays it: one graph launch advances
+ * every member by two steps. Members stay ordinary handles (read them with
+ * pibm_read_fields etc. after pibm_ensemble_status); stepping a member on its
+ * own between ensemble steps is allowed (the graph is rebuilt when needed). All
+ * members must live on one device; the ensemble does not own them and must be
+ * destroyed before them. Errors: PIBM_EINVAL (no members, NULL or repeated
+ * member, members on different devices), PIBM_ECUDA. */
+typedef struct pibm_ensemble_t pibm_ensemble_t;
+int pibm_ensemble_create(pibm_t* const* members, int count, void* stream, pibm_ensemble_t** out);
+int pibm_ensemble_step(pibm_ensemble_t* e, int64_t nsteps);
+/* Synchronise the ensemble's stream; the first non-OK member health status. */
+int pibm_ensemble_status(pibm_ensemble_t* e);
+void pibm_ensemble_destroy(pibm_ensemble_t* e);
+
 /* Free the handle (and the workspace when the library allocated it). NULL is a no-op. */
 void pibm_destroy(pibm_t* h);
 

@@ -32,7 +32,8 @@ NFIELDS = 5
 EXPORTS = ["pibm_workspace_bytes", "pibm_create", "pibm_step", "pibm_forces",
            "pibm_read_fields", "pibm_invariants", "pibm_status", "pibm_kernels_per_step",
            "pibm_destroy", "pibm_strerror", "pibm_profile_steps", "pibm_last_error",
-           "pibm_fluid_sums_noalloc"]
+           "pibm_fluid_sums_noalloc", "pibm_autotune", "pibm_ensemble_create",
+           "pibm_ensemble_step", "pibm_ensemble_status", "pibm_ensemble_destroy"]
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -105,6 +106,16 @@ def load(path: str = LIB_PATH):
     L.pibm_strerror.restype = ctypes.c_char_p
     L.pibm_fluid_sums_noalloc.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), vp, vp]
     L.pibm_fluid_sums_noalloc.restype = ctypes.c_int
+    L.pibm_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.pibm_autotune.restype = ctypes.c_int
+    L.pibm_ensemble_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.POINTER(vp)]
+    L.pibm_ensemble_create.restype = ctypes.c_int
+    L.pibm_ensemble_step.argtypes = [vp, ctypes.c_int64]
+    L.pibm_ensemble_step.restype = ctypes.c_int
+    L.pibm_ensemble_status.argtypes = [vp]
+    L.pibm_ensemble_status.restype = ctypes.c_int
+    L.pibm_ensemble_destroy.argtypes = [vp]
+    L.pibm_ensemble_destroy.restype = None
     L.pibm_last_error.argtypes = []
     L.pibm_last_error.restype = ctypes.c_char_p
     _lib = L

@@ -584,6 +584,236 @@ int pibm_status(pibm_t* h) {
 
 int pibm_kernels_per_step(pibm_t* h) { return h ? h->kernels_per_step : 0; }
 
+int pibm_autotune(pibm_t* h, int* block_xy) {
+  if (!h) return PIBM_EINVAL;
+  DeviceGuard guard(h->device);
+  State& s = h->s;
+  cudaStream_t st = h->stream;
+  // Candidate block shapes; the 16-bit pair kernel fixes x at one warp.
+  static const int scal[][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {32, 4}, {64, 2}, {128, 1}};
+  static const int pair[][2] = {{32, 2}, {32, 4}, {32, 8}};  // kernels take <= 256 threads
+  const bool pk = collide_uses_pair_kernel(s);
+  const int ncand = pk ? 3 : 7;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return PIBM_ECUDA;
+  }
+  int best = -1;
+  float best_ms = 0.f;
+  const int saved[2] = {s.cblk[0], s.cblk[1]};
+  int rc = PIBM_OK;
+  // Running the collide-stream without advancing the step only rewrites the
+  // partner buffer and clears F, both of which hold nothing between steps.
+  for (int i = 0; i < ncand && rc == PIBM_OK; ++i) {
+    s.cblk[0] = pk ? pair[i][0] : scal[i][0];
+    s.cblk[1] = pk ? pair[i][1] : scal[i][1];
+    cudaError_t le = launch_collide_stream(s, st);
+    if (le != cudaSuccess) {  // a shape this launch cannot take: skip it
+      cudaGetLastError();
+      continue;
+    }
+    if (cudaEventRecord(e0, st) != cudaSuccess) {
+      record_error("cudaEventRecord", cudaGetLastError());
+      rc = PIBM_ECUDA;
+      break;
+    }
+    for (int r = 0; r < 3; ++r)
+      if ((le = launch_collide_stream(s, st)) != cudaSuccess) {
+        record_error("launch_collide_stream", le);
+        rc = PIBM_ECUDA;
+      }
+    float ms = 0.f;
+    cudaError_t te = cudaSuccess;
+    if (rc == PIBM_OK && ((te = cudaEventRecord(e1, st)) != cudaSuccess ||
+                          (te = cudaEventSynchronize(e1)) != cudaSuccess ||
+                          (te = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess)) {
+      record_error("autotune timing", te);
+      rc = PIBM_ECUDA;
+    }
+    if (rc != PIBM_OK) break;
+    if (best < 0 || ms < best_ms) {
+      best = i;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != PIBM_OK || best < 0) {
+    s.cblk[0] = saved[0];
+    s.cblk[1] = saved[1];
+    return rc != PIBM_OK ? rc : PIBM_ECUDA;
+  }
+  s.cblk[0] = pk ? pair[best][0] : scal[best][0];
+  s.cblk[1] = pk ? pair[best][1] : scal[best][1];
+  for (int k = 0; k < 2; ++k)  // graphs captured before hold the old launch shape
+    if (h->graph[k]) {
+      cudaGraphExecDestroy(h->graph[k]);
+      h->graph[k] = nullptr;
+    }
+  if (block_xy) {
+    block_xy[0] = s.cblk[0];
+    block_xy[1] = s.cblk[1];
+  }
+  return health(h);
+}
+
+// ---------------------------------------------------------------------------
+// Ensembles: independent simulations advanced together by one graph launch.
+// ---------------------------------------------------------------------------
+struct pibm_ensemble_t {
+  std::vector<pibm_t*> members;
+  cudaStream_t stream;          // launch stream
+  cudaStream_t origin;          // capture origin
+  std::vector<cudaStream_t> lanes;
+  std::vector<int> parity;      // member parities the graph was captured for
+  cudaGraphExec_t graph;
+  int device;
+};
+
+static int ensemble_capture(pibm_ensemble_t* e) {
+  // Two steps of every member, each member on its own capture stream forked
+  // from and joined back into the origin stream, so the graph's branches are
+  // independent and run concurrently.
+  cudaGraph_t g = nullptr;
+  std::vector<cudaEvent_t> evs;
+  auto ev = [&]() -> cudaEvent_t {
+    cudaEvent_t x = nullptr;
+    if (cudaEventCreateWithFlags(&x, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    evs.push_back(x);
+    return x;
+  };
+  int rc = PIBM_OK;
+  if (cudaStreamBeginCapture(e->origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return PIBM_ECUDA;
+  cudaEvent_t fork = ev();
+  if (!fork || cudaEventRecord(fork, e->origin) != cudaSuccess) rc = PIBM_ECUDA;
+  for (size_t i = 0; i < e->members.size() && rc == PIBM_OK; ++i) {
+    pibm_t* m = e->members[i];
+    cudaStream_t ln = e->lanes[i];
+    if (cudaStreamWaitEvent(ln, fork, 0) != cudaSuccess) {
+      rc = PIBM_ECUDA;
+      break;
+    }
+    const int saved = m->s.cur;
+    rc = enqueue_step(m, ln);
+    if (rc == PIBM_OK) rc = enqueue_step(m, ln);
+    m->s.cur = saved;
+    cudaEvent_t join = ev();
+    if (rc == PIBM_OK && (!join || cudaEventRecord(join, ln) != cudaSuccess ||
+                          cudaStreamWaitEvent(e->origin, join, 0) != cudaSuccess))
+      rc = PIBM_ECUDA;
+  }
+  cudaError_t ee = cudaStreamEndCapture(e->origin, &g);
+  for (auto x : evs)
+    if (x) cudaEventDestroy(x);
+  if (rc != PIBM_OK || ee != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return PIBM_ECUDA;
+  }
+  cudaError_t ie = cudaGraphInstantiate(&e->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    e->graph = nullptr;
+    record_error("cudaGraphInstantiate", ie);
+    return PIBM_ECUDA;
+  }
+  for (size_t i = 0; i < e->members.size(); ++i) e->parity[i] = e->members[i]->s.cur;
+  return PIBM_OK;
+}
+
+int pibm_ensemble_create(pibm_t* const* members, int count, void* stream, pibm_ensemble_t** out) {
+  if (!members || count <= 0 || !out) return PIBM_EINVAL;
+  *out = nullptr;
+  int dev = -1;
+  for (int i = 0; i < count; ++i) {
+    if (!members[i]) return PIBM_EINVAL;
+    if (i == 0) dev = members[i]->device;
+    if (members[i]->device != dev) return PIBM_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (members[j] == members[i]) return PIBM_EINVAL;
+  }
+  DeviceGuard guard(dev);
+  pibm_ensemble_t* e = new (std::nothrow) pibm_ensemble_t();
+  if (!e) return PIBM_ENOMEM;
+  e->members.assign(members, members + count);
+  e->stream = (cudaStream_t)stream;
+  e->parity.assign(count, -1);
+  e->graph = nullptr;
+  e->device = dev;
+  e->origin = nullptr;
+  if (cudaStreamCreateWithFlags(&e->origin, cudaStreamNonBlocking) != cudaSuccess) {
+    delete e;
+    return PIBM_ECUDA;
+  }
+  e->lanes.assign(count, nullptr);
+  for (int i = 0; i < count; ++i)
+    if (cudaStreamCreateWithFlags(&e->lanes[i], cudaStreamNonBlocking) != cudaSuccess) {
+      pibm_ensemble_destroy(e);
+      return PIBM_ECUDA;
+    }
+  // members' own streams must be idle before the ensemble takes over
+  for (int i = 0; i < count; ++i)
+    if (cudaStreamSynchronize(members[i]->stream) != cudaSuccess) {
+      pibm_ensemble_destroy(e);
+      return PIBM_ECUDA;
+    }
+  *out = e;
+  return PIBM_OK;
+}
+
+int pibm_ensemble_step(pibm_ensemble_t* e, int64_t nsteps) {
+  if (!e || nsteps < 0) return PIBM_EINVAL;
+  DeviceGuard guard(e->device);
+  while (nsteps > 0) {
+    if (nsteps >= 2) {
+      bool stale = !e->graph;
+      for (size_t i = 0; i < e->members.size() && !stale; ++i)
+        stale = e->parity[i] != e->members[i]->s.cur;
+      if (stale) {
+        if (e->graph) cudaGraphExecDestroy(e->graph);
+        e->graph = nullptr;
+        int rc = ensemble_capture(e);
+        if (rc != PIBM_OK) return rc;
+      }
+      CK(cudaGraphLaunch(e->graph, e->stream));
+      nsteps -= 2;
+    } else {
+      for (pibm_t* m : e->members) {
+        int rc = enqueue_step(m, e->stream);
+        if (rc != PIBM_OK) return rc;
+      }
+      nsteps -= 1;
+    }
+  }
+  return PIBM_OK;
+}
+
+int pibm_ensemble_status(pibm_ensemble_t* e) {
+  if (!e) return PIBM_EINVAL;
+  DeviceGuard guard(e->device);
+  CK(cudaStreamSynchronize(e->stream));
+  int worst = PIBM_OK;
+  for (pibm_t* m : e->members) {
+    int rc = health(m);
+    if (rc != PIBM_OK && worst == PIBM_OK) worst = rc;
+  }
+  return worst;
+}
+
+void pibm_ensemble_destroy(pibm_ensemble_t* e) {
+  if (!e) return;
+  DeviceGuard guard(e->device);
+  if (e->stream) cudaStreamSynchronize(e->stream);
+  if (e->graph) cudaGraphExecDestroy(e->graph);
+  for (cudaStream_t s : e->lanes)
+    if (s) cudaStreamDestroy(s);
+  if (e->origin) cudaStreamDestroy(e->origin);
+  delete e;
+}
+
 int pibm_profile_steps(pibm_t* h, int64_t nsteps, double* phase_ms) {
   if (!h || nsteps < 0 || !phase_ms) return PIBM_EINVAL;
   DeviceGuard guard(h->device);

@@ -425,6 +425,12 @@ dim3 cell_block(const Geometry& g) {
   return dim3(bx, 256 / bx, 1);
 }
 
+// Block shape of the fused collide-stream: the tuned one when set, else the default.
+dim3 collide_block(const State& s, bool pair) {
+  if (s.cblk[0] > 0 && s.cblk[1] > 0) return dim3(s.cblk[0], s.cblk[1], 1);
+  return pair ? dim3(32, 8, 1) : cell_block(s.geo);
+}
+
 template <int Q, class St, typename FT>
 cudaError_t collide_stream_t(const State& s, cudaStream_t st) {
   const Geometry& g = s.geo;
@@ -432,7 +438,7 @@ cudaError_t collide_stream_t(const State& s, cudaStream_t st) {
   using R = typename St::R;
   if constexpr (sizeof(T) == 2) {
     if ((g.n[0] & 1) == 0) {
-      dim3 blk(32, 8, 1);
+      dim3 blk = collide_block(s, true);  // blk.x is 32: one warp per 64 cells of a row
       dim3 grd((g.n[0] + 63) / 64, (g.n[1] + blk.y - 1) / blk.y, g.n[2]);
       k_collide_stream_pair<Q, St, FT><<<grd, blk, 0, st>>>(
           (const T*)s.f[s.cur], (T*)s.f[1 - s.cur], (FT*)s.F, g, (R)s.phy.omega, (R)s.phy.cF,
@@ -440,7 +446,7 @@ cudaError_t collide_stream_t(const State& s, cudaStream_t st) {
       return cudaGetLastError();
     }
   }
-  dim3 blk = cell_block(g);
+  dim3 blk = collide_block(s, false);
   dim3 grd((g.n[0] + blk.x - 1) / blk.x, (g.n[1] + blk.y - 1) / blk.y, g.n[2]);
   k_collide_stream<Q, St, FT><<<grd, blk, 0, st>>>((const T*)s.f[s.cur], (T*)s.f[1 - s.cur],
                                                    (FT*)s.F, g, (R)s.phy.omega, (R)s.phy.cF,
@@ -487,6 +493,10 @@ struct QOf<Lattice<19>> {
 };
 
 }  // namespace
+
+bool collide_uses_pair_kernel(const State& s) {
+  return (s.precision == PIBM_FP16 || s.precision == PIBM_BF16) && (s.geo.n[0] & 1) == 0;
+}
 
 cudaError_t launch_collide_stream(const State& s, cudaStream_t st) {
   return dispatch(s, [&](auto lat, auto store, auto ft) {

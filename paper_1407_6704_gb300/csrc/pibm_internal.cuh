@@ -282,6 +282,7 @@ struct State {
   unsigned* err;  // device health word
   Particles p;
   int cur;        // index of the buffer holding the current f* / X / U
+  int cblk[2];    // collide-stream block shape (x, y); 0 = built-in choice
 };
 
 // ---------------------------------------------------------------------------
@@ -290,6 +291,9 @@ struct State {
 // Fluid: one fused pull-stream + Guo-forced BGK collision, f[cur] -> f[1-cur];
 // consumes F and leaves it zero.
 cudaError_t launch_collide_stream(const State& s, cudaStream_t st);
+// True when the collide-stream runs the two-cells-per-thread 16-bit kernel
+// (its block is 32 wide); the autotuner picks only the block height then.
+bool collide_uses_pair_kernel(const State& s);
 // Write plane a of the stored buffer f[cur] from FP64 values src (already
 // un-streamed by the host), or from the rest value w_a when src is NULL.
 cudaError_t launch_store_plane(const State& s, int a, const double* src, cudaStream_t st);

@@ -13,6 +13,9 @@ Workload presets mirror the sedimentation set-ups used for measurement:
   c3  3D D3Q19 256^3, walls, tau 0.55, 4M particles d=0.6, ratio 2, top half, 4-point
   c3s the 64^3 slice of c3 with the same particle density (62,500 particles)
   c5  3D D3Q19 96^3, walls, tau 0.7, 20k particles d=0.5, ratio 2, top half, 4-point
+  c4  (ensemble_workloads) 64 independent 2D instances, sides log-uniform in
+      [64, 512], 100..20k particles (at most 30 % area of the top half), tau in
+      [0.55, 1.0], ratio in [1.5, 3.0], d = 0.5, 2-point delta
 Contacts: linear spring-dashpot, kn = 1e-2, restitution 0.9, everywhere.
 """
 from dataclasses import dataclass, field
@@ -151,6 +154,28 @@ def sample_particles(n: Sequence[int], n_particles: int, diameter, density_ratio
     if not placed.all():
         raise RuntimeError(f"could not place {np.count_nonzero(~placed)} particles")
     return X, dia, rr
+
+
+def ensemble_workloads(count=64, seed=4, side=(64, 512), particles=(100, 20_000), tau=(0.55, 1.0),
+                       ratio=(1.5, 3.0), diameter=0.5, max_area_fraction=0.3):
+    """The batched ensemble: ``count`` independent 2D sedimentation instances
+    (D2Q9, walls, gravity 1e-5, 2-point delta, d = 0.5): square sides
+    log-uniform in ``side``, particle counts log-uniform in ``particles`` but at
+    most ``max_area_fraction`` of the top half's area, tau and density ratio
+    uniform in their ranges. Returns (Workload, (X, diameter, ratio)) pairs."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        s_ = int(round(np.exp(rng.uniform(np.log(side[0]), np.log(side[1])))))
+        np_ = int(round(np.exp(rng.uniform(np.log(particles[0]), np.log(particles[1])))))
+        cap = int(max_area_fraction * (s_ * s_ / 2.0) / (np.pi * diameter ** 2 / 4.0))
+        np_ = min(np_, cap)
+        t_ = float(rng.uniform(*tau))
+        r_ = float(rng.uniform(*ratio))
+        w = Workload(f"c4.{i}", 9, (s_, s_), (0, 0), t_, 2, (0.0, -1e-5), np_, diameter, r_,
+                     (0.5, 1.0), 1000 + i, steps=2000)
+        out.append((w, workload_particles(w)))
+    return out
 
 
 def workload_particles(w: Workload, n_particles: Optional[int] = None):

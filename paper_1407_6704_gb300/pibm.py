@@ -103,6 +103,12 @@ class Pibm:
     def status(self):
         return self._L.pibm_status(self._h)
 
+    def autotune(self):
+        """Pick the stream-collide block shape by timing; returns (bx, by)."""
+        out = (ctypes.c_int * 2)()
+        check(self._L.pibm_autotune(self._h, out), "pibm_autotune")
+        return out[0], out[1]
+
     @property
     def kernels_per_step(self):
         return self._L.pibm_kernels_per_step(self._h)
@@ -176,3 +182,45 @@ class Pibm:
         return cls(lat, w.n, w.periodic, w.tau, gravity=w.gravity, delta_width=w.delta_width,
                    precision=precision, kn=w.kn, restitution=w.restitution, x0=X, diameter=dia,
                    density_ratio=rr, f0=f0, **kw)
+
+
+class Ensemble:
+    """Independent simulations advanced together: one CUDA graph launch steps
+    every member twice (one graph branch per member)."""
+
+    def __init__(self, members, stream=None):
+        import torch
+
+        self.members = list(members)
+        self._L = _lib.load()
+        arr = (ctypes.c_void_p * len(self.members))(*[m._h.value for m in self.members])
+        self.stream = stream if stream is not None else self.members[0].stream
+        h = ctypes.c_void_p()
+        check(self._L.pibm_ensemble_create(arr, len(self.members),
+                                           ctypes.c_void_p(self.stream.cuda_stream),
+                                           ctypes.byref(h)), "pibm_ensemble_create")
+        self._h = h
+        self._torch = torch
+
+    def step(self, nsteps=1):
+        check(self._L.pibm_ensemble_step(self._h, int(nsteps)), "pibm_ensemble_step")
+
+    def status(self):
+        return self._L.pibm_ensemble_status(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.pibm_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
