@@ -28,6 +28,13 @@ class OrParams(ctypes.Structure):
         ("gravity", ctypes.c_double * 3),
         ("kn", ctypes.c_double),
         ("restitution", ctypes.c_double),
+        ("interp", ctypes.c_int),
+        ("contact", ctypes.c_int),
+        ("young", ctypes.c_double),
+        ("poisson", ctypes.c_double),
+        ("wall_young", ctypes.c_double),
+        ("wall_poisson", ctypes.c_double),
+        ("substeps", ctypes.c_int),
     ]
 
 
@@ -43,6 +50,8 @@ def lib():
         L.or_phi.argtypes = [ctypes.c_int, ctypes.c_double]
         L.or_phi.restype = ctypes.c_double
         L.or_taps.argtypes = [P, ctypes.c_int, ctypes.c_double, ip, dp]
+        L.or_lagrange_taps.argtypes = [P, ctypes.c_int, ctypes.c_double, ip, dp]
+        L.or_interp_taps.argtypes = [P, ctypes.c_int, ctypes.c_double, ip, dp]
         L.or_moments.argtypes = [P, dp, dp, dp]
         L.or_interp_pops.argtypes = [P, dp, dp, dp]
         L.or_contact_force.argtypes = [P, ctypes.c_long, dp, dp, dp, dp, ctypes.c_long, dp]
@@ -89,7 +98,13 @@ class Oracle:
 
     def __init__(self, q, n, periodic, tau, delta_width=2, implicit_drag=True,
                  gravity=(0.0, 0.0, 0.0), kn=1e-2, restitution=0.9,
-                 x0=None, u0=None, diameter=None, density_ratio=None, f0=None):
+                 x0=None, u0=None, diameter=None, density_ratio=None, f0=None,
+                 interp="delta", contact="linear", young=1.0, poisson=0.3, wall_young=None,
+                 wall_poisson=None, substeps=1):
+        """interp: "delta" (the spreading kernel) or "lagrange4" (Eq. 5);
+        contact: "linear" (k_n, e) or "hertz" (Eq. 15 with young/poisson of the
+        particles and of the walls, default the particles' material, and e);
+        substeps: DEM sub-steps per fluid step."""
         self.q = int(q)
         self.d, self.e, self.w, self.opp = lattice(self.q)
         n = list(n) + [1] * (3 - len(n))
@@ -100,7 +115,13 @@ class Oracle:
         self.params = OrParams(self.q, (ctypes.c_int * 3)(*n), (ctypes.c_int * 3)(*per),
                                float(tau), int(delta_width), int(bool(implicit_drag)),
                                (ctypes.c_double * 3)(*(list(gravity) + [0.0] * 3)[:3]),
-                               float(kn), float(restitution))
+                               float(kn), float(restitution),
+                               {"delta": 0, "lagrange4": 1}[interp],
+                               {"linear": 0, "hertz": 1}[contact], float(young), float(poisson),
+                               float(young if wall_young is None else wall_young),
+                               float(poisson if wall_poisson is None else wall_poisson),
+                               int(substeps))
+        self.substeps = int(substeps)
         self.shape = (n[1], n[0]) if self.d == 2 else (n[2], n[1], n[0])
         self.ncell = n[0] * n[1] * n[2]
         if f0 is None:
@@ -148,9 +169,17 @@ class Oracle:
         return rho, j
 
     def taps(self, axis, X):
+        """Spreading taps (Eqs. 10-11) along one axis: (indices, weights)."""
         idx = (ctypes.c_int * 4)()
         w = np.zeros(4)
         cnt = lib().or_taps(ctypes.byref(self.params), int(axis), float(X), idx, _p(w))
+        return [idx[i] for i in range(cnt)], w[:cnt].copy()
+
+    def interp_taps(self, axis, X):
+        """Interpolation taps of the configured interpolant along one axis."""
+        idx = (ctypes.c_int * 4)()
+        w = np.zeros(4)
+        cnt = lib().or_interp_taps(ctypes.byref(self.params), int(axis), float(X), idx, _p(w))
         return [idx[i] for i in range(cnt)], w[:cnt].copy()
 
     def interp_pops(self, X):
@@ -167,6 +196,7 @@ class Oracle:
 
     def particle_update(self, i):
         """(X', U', g, Fc, |g_literal - g_closed|, escaped) for particle i from the current state."""
+        assert self.substeps <= 1, "sampled evaluation covers steps without sub-cycling"
         Xn, Un, g, Fc = (np.zeros(self.d) for _ in range(4))
         dv = np.zeros(1)
         esc = lib().or_particle_update(ctypes.byref(self.params), _p(self.f), self.np, _p(self.X),
@@ -194,12 +224,14 @@ class Oracle:
 
     # --- sampled evaluation of one step (large lattices) ---------------------
     def force_at_cell(self, cell):
+        assert self.substeps <= 1, "sampled evaluation covers steps without sub-cycling"
         out = np.zeros(self.d)
         lib().or_force_at_cell(ctypes.byref(self.params), _p(self.f), self.np, _p(self.X),
                                _p(self.U), _p(self.dia), _p(self.rr), int(cell), _p(out))
         return out
 
     def cell_after_step(self, cell):
+        assert self.substeps <= 1, "sampled evaluation covers steps without sub-cycling"
         out = np.zeros(self.q)
         lib().or_cell_after_step(ctypes.byref(self.params), _p(self.f), self.np, _p(self.X),
                                  _p(self.U), _p(self.dia), _p(self.rr), int(cell), _p(out))

@@ -12,7 +12,8 @@
  *   (1) velocity set, (2) BGK update, (3) equilibrium, (4) interpolation to a
  *   particle, (5) Lagrange interpolant, (6) moving bounce-back, (7) force
  *   density, (8) body-force term, (9) spreading, (10) discrete delta,
- *   (11) one-dimensional kernel, (12) reaction force, (13) translation ODE.
+ *   (11) one-dimensional kernel, (12) reaction force, (13) translation ODE,
+ *   (15) Hertz normal force-displacement law.
  *
  * Frame and readings used throughout (the paper is silent on them):
  *  - lattice units, h = 1, dt = 1, c = 1, c_s^2 = 1/3;
@@ -27,11 +28,21 @@
  *    (Eq. 9), collide every cell with the Guo term (Eqs. 2, 3, 8), stream;
  *  - Eq. (7) is read as the momentum exchange sum_beta e_beta [f_beta(new) -
  *    f_beta(old)] at the particle, which equals 2 (rho_l U - j_l);
- *  - the interpolation weights are the same per-axis kernel as the spreading
- *    (2-point hat or the 4-point cosine of Eq. 11); taps that fall outside a
- *    wall axis are dropped and the remaining weights are renormalised per axis;
- *  - contacts: linear spring-dashpot normal force (k_n, restitution e), brute
- *    force over all pairs, plus the walls; no tangential force, no rotation.
+ *  - the interpolation weights are, by default, the same per-axis kernel as the
+ *    spreading (2-point hat or the 4-point cosine of Eq. 11); taps that fall
+ *    outside a wall axis are dropped and the remaining weights are renormalised
+ *    per axis. The alternative (interp = 1) is the 4-point Lagrange polynomial
+ *    of Eq. (5) over a 4-node block per axis, shifted to lie inside the domain
+ *    next to a wall (one-sided, an extrapolation there as the paper describes);
+ *  - contacts: linear spring-dashpot normal force (k_n, restitution e) by
+ *    default, or (contact = 1) the Hertz law of Eq. (15) with the damping of the
+ *    Hertz-Mindlin model of Tsuji et al. (1992) for the same restitution
+ *    coefficient; brute force over all pairs, plus the walls; no tangential
+ *    force, no rotation;
+ *  - DEM sub-cycling (substeps S > 1): the interpolated rho_l, j_l stay fixed
+ *    for the fluid step, the contact forces and the particle update run S
+ *    times with h = 1/S, and the fluid receives the time average of the force
+ *    density; S = 1 is the plain step.
  *
  * Layouts: populations f[a * ncell + c], c = x + nx * (y + ny * z);
  * force F[k * ncell + c]; particle vectors are AoS with d components.
@@ -54,6 +65,11 @@ typedef struct {
   double gravity[3];  /* acceleration acting on particles */
   double kn;          /* contact spring stiffness */
   double restitution; /* normal restitution coefficient */
+  int interp;         /* 0: same kernel as the spreading; 1: 4-point Lagrange, Eq. (5) */
+  int contact;        /* 0: linear spring-dashpot; 1: Hertz, Eq. (15) */
+  double young, poisson;           /* particle material (Hertz) */
+  double wall_young, wall_poisson; /* wall material (Hertz) */
+  int substeps;       /* DEM sub-steps per fluid step; <= 1 means 1 */
 } or_params;
 
 typedef struct {
@@ -166,6 +182,40 @@ int or_taps(const or_params* p, int axis, double X, int* idx, double* w) {
   return cnt;
 }
 
+/* Eq. (5) along one axis: the 4-point Lagrange interpolant. The block is the
+ * nodes first .. first + 3, first = floor(X - 1/2) - 1 (two nodes on each side
+ * of X); on a wall axis it is shifted to lie inside [0, N - 1] (needs N >= 4),
+ * on a periodic axis the indices wrap. Weight of node t, at x_t = first + t +
+ * 1/2: the product over the other nodes l of (X - x_l) / (x_t - x_l). */
+int or_lagrange_taps(const or_params* p, int axis, double X, int* idx, double* w) {
+  int N = p->n[axis];
+  int first = (int)floor(X - 0.5) - 1;
+  if (!p->periodic[axis]) {
+    if (first < 0) first = 0;
+    if (first > N - 4) first = N - 4;
+  }
+  for (int t = 0; t < 4; ++t) {
+    double xt = (double)(first + t) + 0.5;
+    double L = 1.0;
+    for (int l = 0; l < 4; ++l) {
+      if (l == t) continue;
+      double xl = (double)(first + l) + 0.5;
+      L *= (X - xl) / (xt - xl);
+    }
+    int k = first + t;
+    idx[t] = p->periodic[axis] ? ((k % N) + N) % N : k;
+    w[t] = L;
+  }
+  return 4;
+}
+
+/* The interpolation taps of the configured interpolant (Eq. 4 with Eq. 5 or
+ * with the spreading kernel). */
+int or_interp_taps(const or_params* p, int axis, double X, int* idx, double* w) {
+  if (p->interp == 1) return or_lagrange_taps(p, axis, X, idx, w);
+  return or_taps(p, axis, X, idx, w);
+}
+
 /* Macroscopic moments of the stored populations: rho = sum f, j = sum e f. */
 void or_moments(const or_params* p, const double* f, double* rho, double* j) {
   or_lattice_t L;
@@ -184,7 +234,7 @@ void or_moments(const or_params* p, const double* f, double* rho, double* j) {
 }
 
 /* Eq. (4): every population interpolated to the particle position X with the
- * tensor-product weights of the per-axis taps. */
+ * tensor-product weights of the per-axis interpolation taps. */
 void or_interp_pops(const or_params* p, const double* f, const double* X, double* fl) {
   or_lattice_t L;
   or_lattice_get(p->q, &L);
@@ -193,7 +243,7 @@ void or_interp_pops(const or_params* p, const double* f, const double* X, double
   double w[3][4];
   idx[2][0] = 0;
   w[2][0] = 1.0;
-  for (int k = 0; k < L.d; ++k) cnt[k] = or_taps(p, k, X[k], idx[k], w[k]);
+  for (int k = 0; k < L.d; ++k) cnt[k] = or_interp_taps(p, k, X[k], idx[k], w[k]);
   for (int a = 0; a < L.q; ++a) fl[a] = 0.0;
   for (int tz = 0; tz < cnt[2]; ++tz)
     for (int ty = 0; ty < cnt[1]; ++ty)
@@ -221,9 +271,28 @@ static double or_sep(const or_params* p, int k, double a, double b) {
   return s;
 }
 
-/* Contact force on particle i: linear spring-dashpot along the normal, summed
- * over every other particle (brute force, ascending index) and over the walls.
- * gamma = 2 beta sqrt(m_eff kn), beta = -ln e / sqrt(pi^2 + ln^2 e). */
+/* Magnitude of the normal contact force (positive = repulsive) for an overlap
+ * delta > 0 and a normal relative velocity vn (positive = separating), with
+ * reduced mass meff, effective radius Rs and effective modulus Es.
+ * Linear: k_n delta - gamma vn, gamma = 2 beta sqrt(meff k_n).
+ * Hertz, Eq. (15): (4/3) Es sqrt(Rs) delta^{3/2}, damped by gamma vn with
+ * gamma = 2 sqrt(5/6) beta sqrt(S_n meff), S_n = 2 Es sqrt(Rs delta) the
+ * contact stiffness (Tsuji et al. 1992). beta = -ln e / sqrt(pi^2 + ln^2 e). */
+static double or_normal_force(const or_params* p, double beta, double delta, double vn,
+                              double meff, double Rs, double Es) {
+  if (p->contact == 1) {
+    double Sn = 2.0 * Es * sqrt(Rs * delta);
+    double gam = 2.0 * sqrt(5.0 / 6.0) * beta * sqrt(Sn * meff);
+    return (4.0 / 3.0) * Es * sqrt(Rs) * pow(delta, 1.5) - gam * vn;
+  }
+  double gam = 2.0 * beta * sqrt(meff * p->kn);
+  return p->kn * delta - gam * vn;
+}
+
+/* Contact force on particle i, summed over every other particle (brute force,
+ * ascending index) and over the walls, along the normal. Effective radius
+ * 1/R* = 1/R_1 + 1/R_2 (R* = R_i against a wall) and modulus
+ * 1/E* = (1 - nu_1^2)/E_1 + (1 - nu_2^2)/E_2 (Eq. 15). */
 void or_contact_force(const or_params* p, long np, const double* X, const double* U,
                       const double* dia, const double* rr, long i, double* Fc) {
   int d = (p->q == 9) ? 2 : 3;
@@ -231,6 +300,12 @@ void or_contact_force(const or_params* p, long np, const double* X, const double
   double beta = -lne / sqrt(OR_PI * OR_PI + lne * lne);
   double mi = or_mass(d, dia[i], rr[i]);
   double ri = 0.5 * dia[i];
+  double cp = 0.0, Epp = 0.0, Epw = 0.0;
+  if (p->contact == 1) {
+    cp = (1.0 - p->poisson * p->poisson) / p->young;
+    Epp = 1.0 / (cp + cp);
+    Epw = 1.0 / (cp + (1.0 - p->wall_poisson * p->wall_poisson) / p->wall_young);
+  }
   for (int k = 0; k < d; ++k) Fc[k] = 0.0;
   for (long jx = 0; jx < np; ++jx) {
     if (jx == i) continue;
@@ -240,29 +315,29 @@ void or_contact_force(const or_params* p, long np, const double* X, const double
       dist2 += s[k] * s[k];
     }
     double dist = sqrt(dist2);
-    double delta = ri + 0.5 * dia[jx] - dist;
+    double rj = 0.5 * dia[jx];
+    double delta = ri + rj - dist;
     if (delta <= 0.0 || dist <= 0.0) continue;
     double mj = or_mass(d, dia[jx], rr[jx]);
     double meff = mi * mj / (mi + mj);
-    double gam = 2.0 * beta * sqrt(meff * p->kn);
     double vn = 0.0;
     for (int k = 0; k < d; ++k) vn += (U[i * d + k] - U[jx * d + k]) * (s[k] / dist);
-    double mag = p->kn * delta - gam * vn;
+    double mag = or_normal_force(p, beta, delta, vn, meff, ri * rj / (ri + rj), Epp);
     for (int k = 0; k < d; ++k) Fc[k] += mag * (s[k] / dist);
   }
-  double gw = 2.0 * beta * sqrt(mi * p->kn);
   for (int k = 0; k < d; ++k) {
     if (p->periodic[k]) continue;
     /* wall at 0, normal +e_k */
     double delta = ri - X[i * d + k];
-    if (delta > 0.0) Fc[k] += p->kn * delta - gw * U[i * d + k];
+    if (delta > 0.0) Fc[k] += or_normal_force(p, beta, delta, U[i * d + k], mi, ri, Epw);
     /* wall at N, normal -e_k */
     delta = ri - ((double)p->n[k] - X[i * d + k]);
-    if (delta > 0.0) Fc[k] -= p->kn * delta - gw * (-U[i * d + k]);
+    if (delta > 0.0) Fc[k] -= or_normal_force(p, beta, delta, -U[i * d + k], mi, ri, Epw);
   }
 }
 
-/* Particle phase for particle i (§2.2-2.3), from the step-n state:
+/* Particle phase for particle i (§2.2-2.3) without sub-cycling (S = 1), from
+ * the step-n state:
  * outputs X^{n+1}, U^{n+1}, the force density g (Eq. 7) and the contact force.
  * diag[0] receives |g_literal - 2 (rho_l U - j_l)| (max over components).
  * Returns 1 if the particle left the domain through a wall, else 0. */
@@ -433,17 +508,102 @@ void or_stream(const or_params* p, const double* fs, double* f) {
  * state. F receives the spread force of this step; g, Fc the per-particle
  * force density and contact force. diag[0]: max literal-vs-closed g deviation;
  * diag[1]: number of escaped particles. */
+/* Particle phase of all particles with S = substeps DEM sub-steps of length
+ * h = 1/S. rho_l, j_l are interpolated once at the step-n positions (Eq. 4);
+ * each sub-step takes the contact forces of all particles at the sub-step
+ * state and then advances every particle:
+ *   implicit: m (U' - U) = h [buoy g + Fc - 2 A_p (rho_l U' - j_l)],
+ *   explicit: m (U' - U) = h [buoy g + Fc - 2 A_p (rho_l U - j_l)],
+ *   X' = X + h U'.
+ * g (to the fluid) and Fc (reported) are the averages over the sub-steps of
+ * 2 (rho_l U_b - j_l) and of the contact force. Returns the number of
+ * sub-step moves that left the domain through a wall. */
+static double or_particles_subcycled(const or_params* p, const double* f, long np,
+                                     const double* X, const double* U, const double* dia,
+                                     const double* rr, double* Xn, double* Un, double* g,
+                                     double* Fc) {
+  or_lattice_t L;
+  or_lattice_get(p->q, &L);
+  int d = L.d;
+  int S = p->substeps;
+  double h = 1.0 / (double)S;
+  double* rho = (double*)malloc(sizeof(double) * np);
+  double* jl = (double*)malloc(sizeof(double) * np * d);
+  double* Xs = (double*)malloc(sizeof(double) * np * d);
+  double* Us = (double*)malloc(sizeof(double) * np * d);
+  double* Fs = (double*)malloc(sizeof(double) * np * d);
+  double esc = 0.0;
+  for (long i = 0; i < np; ++i) {
+    double fl[OR_MAXQ];
+    or_interp_pops(p, f, X + i * d, fl);
+    rho[i] = 0.0;
+    for (int k = 0; k < d; ++k) jl[i * d + k] = 0.0;
+    for (int a = 0; a < L.q; ++a) {
+      rho[i] += fl[a];
+      for (int k = 0; k < d; ++k) jl[i * d + k] += L.e[a][k] * fl[a];
+    }
+  }
+  memcpy(Xs, X, sizeof(double) * np * d);
+  memcpy(Us, U, sizeof(double) * np * d);
+  memset(g, 0, sizeof(double) * np * d);
+  memset(Fc, 0, sizeof(double) * np * d);
+  for (int sub = 0; sub < S; ++sub) {
+    for (long i = 0; i < np; ++i) or_contact_force(p, np, Xs, Us, dia, rr, i, Fs + i * d);
+    for (long i = 0; i < np; ++i) {
+      double m = or_mass(d, dia[i], rr[i]);
+      double Ap = OR_PI * dia[i] * dia[i] / 4.0;
+      double buoy = m * (1.0 - 1.0 / rr[i]);
+      for (int k = 0; k < d; ++k) {
+        double Uo = Us[i * d + k], Ub;
+        double fc = Fs[i * d + k];
+        if (p->implicit_drag) {
+          Un[i * d + k] = (m * Uo + h * (2.0 * Ap * jl[i * d + k] + buoy * p->gravity[k] + fc)) /
+                          (m + 2.0 * Ap * rho[i] * h);
+          Ub = Un[i * d + k];
+        } else {
+          Un[i * d + k] =
+              Uo + h * (buoy * p->gravity[k] + fc - Ap * 2.0 * (rho[i] * Uo - jl[i * d + k])) / m;
+          Ub = Uo;
+        }
+        g[i * d + k] += h * 2.0 * (rho[i] * Ub - jl[i * d + k]);
+        Fc[i * d + k] += h * fc;
+        double x = Xs[i * d + k] + h * Un[i * d + k];
+        if (p->periodic[k]) {
+          double N = (double)p->n[k];
+          if (x < 0.0) x += N;
+          else if (x >= N) x -= N;
+        } else if (x < 0.0 || x > (double)p->n[k]) {
+          esc += 1.0;
+        }
+        Xn[i * d + k] = x;
+      }
+    }
+    memcpy(Xs, Xn, sizeof(double) * np * d);
+    memcpy(Us, Un, sizeof(double) * np * d);
+  }
+  free(rho);
+  free(jl);
+  free(Xs);
+  free(Us);
+  free(Fs);
+  return esc;
+}
+
 void or_step(const or_params* p, double* f, double* fs, double* F, long np, double* X, double* U,
              const double* dia, const double* rr, double* Xn, double* Un, double* g, double* Fc,
              double* diag) {
   int d = (p->q == 9) ? 2 : 3;
   long nc = or_ncell(p);
   double dev_max = 0.0, esc = 0.0;
-  for (long i = 0; i < np; ++i) {
-    double dv = 0.0;
-    esc += or_particle_update(p, f, np, X, U, dia, rr, i, Xn + i * d, Un + i * d, g + i * d,
-                              Fc + i * d, &dv);
-    if (dv > dev_max) dev_max = dv;
+  if (p->substeps > 1) {
+    esc = or_particles_subcycled(p, f, np, X, U, dia, rr, Xn, Un, g, Fc);
+  } else {
+    for (long i = 0; i < np; ++i) {
+      double dv = 0.0;
+      esc += or_particle_update(p, f, np, X, U, dia, rr, i, Xn + i * d, Un + i * d, g + i * d,
+                                Fc + i * d, &dv);
+      if (dv > dev_max) dev_max = dv;
+    }
   }
   memset(F, 0, sizeof(double) * d * nc);
   for (long i = 0; i < np; ++i) or_spread_one(p, X + i * d, dia[i], g + i * d, F);
