@@ -53,7 +53,8 @@ extern "C" {
 #define PIBM_EINVAL (-1)    /* bad argument or configuration */
 #define PIBM_ENOMEM (-2)    /* workspace too small or allocation failed */
 #define PIBM_ECUDA (-3)     /* a CUDA call failed */
-#define PIBM_EUNSTABLE (-4) /* non-finite fluid or particle state detected */
+#define PIBM_EUNSTABLE (-4) /* non-finite fluid or particle state detected, or a particle
+                               moved too far within one sub-cycled step */
 #define PIBM_EESCAPED (-5)  /* a particle crossed a wall */
 #define PIBM_ENOTSUP (-6)   /* combination not built into this library */
 #define PIBM_EINTERNAL (-7) /* a device-side index check failed; the access was skipped */
@@ -71,6 +72,20 @@ extern "C" {
 /* particle drag coupling */
 #define PIBM_IMPLICIT 0 /* force density evaluated with U^{n+1} (solved in closed form) */
 #define PIBM_EXPLICIT 1 /* force density evaluated with U^n */
+
+/* interpolation of the fluid to the particles (Eq. 4) */
+#define PIBM_INTERP_DELTA 0     /* the spreading kernel (delta_width), renormalised at walls */
+#define PIBM_INTERP_LAGRANGE4 1 /* Eq. (5): 4-point Lagrange polynomials per axis over the
+                                   nodes floor(X - 1/2) - 1 .. + 2, the block shifted inside
+                                   the domain next to a wall; spreading keeps delta_width */
+
+/* normal contact law */
+#define PIBM_DEM_LINEAR 0 /* k_n delta - gamma v_n, gamma = 2 beta sqrt(m_eff k_n) */
+#define PIBM_DEM_HERTZ 1  /* Eq. (15): (4/3) E* sqrt(R*) delta^{3/2} - gamma v_n,
+                             gamma = 2 sqrt(5/6) beta sqrt(2 E* sqrt(R* delta) m_eff);
+                             1/E* = (1 - nu_1^2)/E_1 + (1 - nu_2^2)/E_2, 1/R* = 1/R_1 + 1/R_2
+                             (R* = R against a wall); beta from dem_restitution as for
+                             the linear law */
 
 /* storage / arithmetic of the populations; particles, contacts and the
  * particle integration are FP64 in every mode */
@@ -111,6 +126,24 @@ typedef struct pibm_config {
   const double* density_ratio; /* host, [n_particles], rho_p / rho_f, > 0 */
   const double* f0;    /* host, [q][ncell] post-stream populations of step 0, or
                           NULL for the rest state f_a = w_a (rho = 1, u = 0) */
+  /* Variants of the paper's method; a zero-initialised tail selects the
+   * defaults (interpolation with the spreading kernel, linear contacts, no
+   * sub-cycling). */
+  int interp;          /* PIBM_INTERP_DELTA or PIBM_INTERP_LAGRANGE4 (every wall axis
+                          then needs n >= 4) */
+  int dem_model;       /* PIBM_DEM_LINEAR or PIBM_DEM_HERTZ (dem_kn is then unused) */
+  double dem_young;    /* Hertz: Young's modulus of the particles, > 0 (lattice units) */
+  double dem_poisson;  /* Hertz: Poisson ratio of the particles, in [0, 1/2) */
+  double wall_young;   /* Hertz: Young's modulus of the walls; 0 = the particles' */
+  double wall_poisson; /* Hertz: Poisson ratio of the walls (used when wall_young > 0) */
+  int dem_substeps;    /* DEM sub-steps S per fluid step (0 or 1: none). With S > 1 the
+                          interpolated rho_l, j_l stay fixed for the step, contacts and
+                          the particle update run S times with h = 1/S, and the fluid
+                          receives the sub-step average of the force density. Every
+                          particle's displacement within one step must stay below
+                          (1 - largest diameter) / 2 so that the cell list of the step
+                          start still holds every pair that can touch; a larger one
+                          raises PIBM_EUNSTABLE. */
 } pibm_config;
 
 typedef struct pibm_t pibm_t; /* opaque handle owning the device state */

@@ -24,6 +24,8 @@ PIBM_D2Q9, PIBM_D3Q15, PIBM_D3Q19 = 9, 15, 19
 PIBM_WALL, PIBM_PERIODIC = 0, 1
 PIBM_IMPLICIT, PIBM_EXPLICIT = 0, 1
 PIBM_FP64, PIBM_FP32, PIBM_FP16, PIBM_BF16 = 0, 1, 2, 3
+PIBM_INTERP_DELTA, PIBM_INTERP_LAGRANGE4 = 0, 1
+PIBM_DEM_LINEAR, PIBM_DEM_HERTZ = 0, 1
 
 FIELD_RHO, FIELD_J, FIELD_POP, FIELD_X, FIELD_U = (1 << k for k in range(5))
 NFIELDS = 5
@@ -57,6 +59,13 @@ class PibmConfig(ctypes.Structure):
         ("diameter", _dp),
         ("density_ratio", _dp),
         ("f0", _dp),
+        ("interp", ctypes.c_int),
+        ("dem_model", ctypes.c_int),
+        ("dem_young", ctypes.c_double),
+        ("dem_poisson", ctypes.c_double),
+        ("wall_young", ctypes.c_double),
+        ("wall_poisson", ctypes.c_double),
+        ("dem_substeps", ctypes.c_int),
     ]
 
 

@@ -35,7 +35,7 @@ constexpr size_t ALIGN = 256;
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-  size_t f, F, mom, red, err, out, X, U, rad, mass, Ap, buoy, gw, radf, xr, cr, xs, cs, g, Fc, key, rank, perm, bin,
+  size_t f, F, mom, red, err, out, X, U, rad, mass, Ap, buoy, gw, cf, pid, rl, jl, Fs, xr, cr, xs, cs, g, Fc, key, rank, perm, bin,
       bsum;
   size_t total;
 };
@@ -90,6 +90,19 @@ int validate(const pibm_config* c) {
   for (int k = 0; k < 3; ++k)
     if (!isfinite(c->gravity[k])) return PIBM_EINVAL;
   if (c->n_particles < 0 || c->n_particles > 0x7fffffffLL) return PIBM_EINVAL;
+  if (c->interp != PIBM_INTERP_DELTA && c->interp != PIBM_INTERP_LAGRANGE4) return PIBM_EINVAL;
+  if (c->interp == PIBM_INTERP_LAGRANGE4)
+    for (int k = 0; k < d; ++k)
+      if (c->boundary[k] == PIBM_WALL && c->n[k] < 4) return PIBM_EINVAL;
+  if (c->dem_model != PIBM_DEM_LINEAR && c->dem_model != PIBM_DEM_HERTZ) return PIBM_EINVAL;
+  if (c->dem_model == PIBM_DEM_HERTZ) {
+    if (!(c->dem_young > 0.0) || !isfinite(c->dem_young)) return PIBM_EINVAL;
+    if (!(c->dem_poisson >= 0.0 && c->dem_poisson < 0.5)) return PIBM_EINVAL;
+    if (!(c->wall_young >= 0.0) || !isfinite(c->wall_young)) return PIBM_EINVAL;
+    if (c->wall_young > 0.0 && !(c->wall_poisson >= 0.0 && c->wall_poisson < 0.5))
+      return PIBM_EINVAL;
+  }
+  if (c->dem_substeps < 0 || c->dem_substeps > 4096) return PIBM_EINVAL;
   if (c->n_particles > 0) {
     if (!c->x0 || !c->diameter || !c->density_ratio) return PIBM_EINVAL;
     for (int k = 0; k < d; ++k)  // contact and spreading stencils must not alias
@@ -137,12 +150,17 @@ Layout layout(const pibm_config* c) {
   L.out = take(sizeof(double) * 8);
   L.X = take(2 * align_up(sizeof(double) * d * np));
   L.U = take(2 * align_up(sizeof(double) * d * np));
-  L.rad = take(sizeof(double) * np);
-  L.mass = take(sizeof(double) * np);
-  L.Ap = take(sizeof(double) * np);
-  L.buoy = take(sizeof(double) * np);
-  L.gw = take(sizeof(double) * np);
-  L.radf = take(sizeof(float) * np);
+  L.rad = take(2 * align_up(sizeof(double) * np));
+  L.mass = take(2 * align_up(sizeof(double) * np));
+  L.Ap = take(2 * align_up(sizeof(double) * np));
+  L.buoy = take(2 * align_up(sizeof(double) * np));
+  L.gw = take(2 * align_up(sizeof(double) * np));
+  L.cf = take(2 * align_up(sizeof(float4) * np));
+  L.pid = take(2 * align_up(sizeof(unsigned) * np));
+  const bool sub = c->dem_substeps > 1;
+  L.rl = take(sub ? sizeof(double) * np : 0);
+  L.jl = take(sub ? sizeof(double) * d * np : 0);
+  L.Fs = take(sub ? sizeof(double) * d * np : 0);
   L.xr = take(sizeof(float4) * np);
   L.cr = take(sizeof(int4) * np);
   L.xs = take(sizeof(float4) * np);
@@ -231,7 +249,7 @@ int health(pibm_t* h) {
   unsigned err = 0;
   CK(cudaMemcpyAsync(&err, h->s.err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  if (err & (ERR_FLUID_NONFINITE | ERR_PARTICLE_NONFINITE)) return PIBM_EUNSTABLE;
+  if (err & (ERR_FLUID_NONFINITE | ERR_PARTICLE_NONFINITE | ERR_SKIN)) return PIBM_EUNSTABLE;
   if (err & ERR_ESCAPED) return PIBM_EESCAPED;
   if (err & ERR_INDEX) return PIBM_EINTERNAL;
   return PIBM_OK;
@@ -330,7 +348,10 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
   s.phy.tau = cfg->tau;
   s.phy.omega = 1.0 / cfg->tau;
   s.phy.cF = 1.0 - 0.5 / cfg->tau;
-  for (int k = 0; k < 3; ++k) s.phy.gravity[k] = k < d ? cfg->gravity[k] : 0.0;
+  for (int k = 0; k < 3; ++k) {
+    s.phy.gravity[k] = k < d ? cfg->gravity[k] : 0.0;
+    s.phy.gravityf[k] = (float)s.phy.gravity[k];
+  }
   s.phy.kn = cfg->dem_kn;
   {
     const double lne = log(cfg->dem_restitution);
@@ -338,6 +359,25 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
   }
   s.phy.width = cfg->delta_width;
   s.phy.implicit_drag = cfg->coupling == PIBM_IMPLICIT;
+  s.phy.lagrange = cfg->interp == PIBM_INTERP_LAGRANGE4;
+  s.phy.hertz = cfg->dem_model == PIBM_DEM_HERTZ;
+  s.phy.Epp = s.phy.Epw = s.phy.hz_damp = 0.0;
+  if (s.phy.hertz) {
+    // 1/E* = (1 - nu_1^2)/E_1 + (1 - nu_2^2)/E_2 (Eq. 15)
+    const double cp = (1.0 - cfg->dem_poisson * cfg->dem_poisson) / cfg->dem_young;
+    const double cw = cfg->wall_young > 0.0
+                          ? (1.0 - cfg->wall_poisson * cfg->wall_poisson) / cfg->wall_young
+                          : cp;
+    s.phy.Epp = 1.0 / (cp + cp);
+    s.phy.Epw = 1.0 / (cp + cw);
+    s.phy.hz_damp = 2.0 * sqrt(5.0 / 6.0) * s.phy.beta;
+  }
+  s.phy.substeps = cfg->dem_substeps > 1 ? cfg->dem_substeps : 1;
+  {
+    double dmax = 0.0;
+    for (long long p = 0; p < cfg->n_particles; ++p) dmax = fmax(dmax, cfg->diameter[p]);
+    s.phy.skin = 0.5 * (1.0 - dmax);
+  }
   s.precision = cfg->precision;
   s.deterministic = cfg->deterministic ? 1 : 0;
   const size_t ts = pop_bytes(cfg->precision);
@@ -358,17 +398,24 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
   P.X[1] = (double*)(base + L.X + xb);
   P.U[0] = (double*)(base + L.U);
   P.U[1] = (double*)(base + L.U + xb);
-  P.rad = (double*)(base + L.rad);
-  P.mass = (double*)(base + L.mass);
-  P.Ap = (double*)(base + L.Ap);
-  P.buoy = (double*)(base + L.buoy);
-  P.gw = (double*)(base + L.gw);
-  P.radf = (float*)(base + L.radf);
+  const size_t db = align_up(sizeof(double) * np), fb = align_up(sizeof(float) * np);
+  for (int b = 0; b < 2; ++b) {
+    P.rad[b] = (double*)(base + L.rad + b * db);
+    P.mass[b] = (double*)(base + L.mass + b * db);
+    P.Ap[b] = (double*)(base + L.Ap + b * db);
+    P.buoy[b] = (double*)(base + L.buoy + b * db);
+    P.gw[b] = (double*)(base + L.gw + b * db);
+    P.cf[b] = (float4*)(base + L.cf + b * align_up(sizeof(float4) * np));
+    P.pid[b] = (unsigned*)(base + L.pid + b * fb);
+  }
   P.xr = (float4*)(base + L.xr);
   P.cr = (int4*)(base + L.cr);
   P.xs = (float4*)(base + L.xs);
   P.cs = (int4*)(base + L.cs);
   P.g = (double*)(base + L.g);
+  P.rl = (double*)(base + L.rl);
+  P.jl = (double*)(base + L.jl);
+  P.Fs = (double*)(base + L.Fs);
   P.Fc = (double*)(base + L.Fc);
   P.key = (unsigned*)(base + L.key);
   P.rank = (unsigned*)(base + L.rank);
@@ -443,17 +490,23 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
         soa[(size_t)k * np + p] = cfg->u0 ? cfg->u0[p * d + k] : 0.0;
     if (cudaMemcpyAsync(P.U[0], soa.data(), sizeof(double) * d * np, cudaMemcpyHostToDevice,
                         st) != cudaSuccess ||
-        cudaMemcpyAsync(P.rad, cfg->diameter, sizeof(double) * np, cudaMemcpyHostToDevice, st) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(P.buoy, cfg->density_ratio, sizeof(double) * np, cudaMemcpyHostToDevice,
+        cudaMemcpyAsync(P.rad[0], cfg->diameter, sizeof(double) * np, cudaMemcpyHostToDevice,
                         st) != cudaSuccess ||
+        cudaMemcpyAsync(P.buoy[0], cfg->density_ratio, sizeof(double) * np,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemsetAsync(P.g, 0, sizeof(double) * d * np, st) != cudaSuccess ||
         cudaMemsetAsync(P.Fc, 0, sizeof(double) * d * np, st) != cudaSuccess ||
         launch_particle_init(s, st) != cudaSuccess)
       return fail(PIBM_ECUDA);
   }
   if (cudaStreamSynchronize(st) != cudaSuccess) return fail(PIBM_ECUDA);
-  h->kernels_per_step = np > 0 ? (s.deterministic ? 11 : 9) : 1;
+  // binning 5 (+1 ordered bins), contacts 1, moments + coupling 2 (+1 ordered
+  // gather), collide 1; with S DEM sub-steps the contacts and the coupling become
+  // 1 + 2 S (+1 spread unless gathered)
+  {
+    const int S = s.phy.substeps, det = s.deterministic;
+    h->kernels_per_step = np == 0 ? 1 : (S <= 1 ? (det ? 11 : 9) : (det ? 10 : 9) + 2 * S);
+  }
   *out = h;
   return PIBM_OK;
 }
@@ -554,11 +607,18 @@ int pibm_read_fields(pibm_t* h, unsigned mask, void* const* dst, int on_device) 
     if (on_device) {
       CK(launch_interleave(s, src, o, st));
     } else {
+      // storage order -> user order on the host
       std::vector<double> soa((size_t)d * np);
+      std::vector<unsigned> pid((size_t)np);
       CK(cudaMemcpyAsync(soa.data(), src, sizeof(double) * d * np, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(pid.data(), s.p.pid[s.cur], sizeof(unsigned) * np,
+                         cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
-      for (long long p = 0; p < np; ++p)
-        for (int k = 0; k < d; ++k) o[p * d + k] = soa[(size_t)k * np + p];
+      for (long long i = 0; i < np; ++i) {
+        const unsigned p = pid[(size_t)i];
+        if (p >= (unsigned long long)np) return PIBM_EINTERNAL;
+        for (int k = 0; k < d; ++k) o[(size_t)p * d + k] = soa[(size_t)k * np + i];
+      }
     }
   }
   return health(h);

@@ -8,8 +8,9 @@
 //   - advances U and X (Eq. 13, with the drag implicit or explicit),
 //   - forms the force density g = 2 (rho_l U - j_l) of the moving bounce-back
 //     (Eqs. 6-7) and spreads A_p g back to the lattice (Eq. 9).
-// Particle state is FP64 structure-of-arrays; positions and velocities are
-// double-buffered so that every contact reads the state of step n.
+// Particle state is FP64 structure-of-arrays, double-buffered so that every
+// contact reads the state of step n, and stored in cell-sorted order: the
+// coupled kernel writes the new state at the particle's slot in the cell list.
 #include <limits.h>
 #include <math.h>
 
@@ -44,7 +45,7 @@ __device__ __forceinline__ unsigned bin_index(const BinMap& b, int x, int y, int
 // contiguous bin range, so after sorting its particles form one contiguous range.
 template <int D>
 __global__ void k_bin_key(const double* __restrict__ X, long long np, Geometry g, BinMap bm,
-                          const float* __restrict__ radf, unsigned* __restrict__ key,
+                          const float4* __restrict__ cf, unsigned* __restrict__ key,
                           unsigned* __restrict__ rank, unsigned* __restrict__ cnt,
                           float4* __restrict__ xr, int4* __restrict__ cr) {
   long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -57,8 +58,8 @@ __global__ void k_bin_key(const double* __restrict__ X, long long np, Geometry g
     b[k] = bin_coord(x, g.n[k]);
     fr[k] = (float)(x - (double)b[k]);  // position inside its cell, exact to FP32
   }
-  xr[p] = make_float4(fr[0], fr[1], fr[2], radf[p]);
-  cr[p] = make_int4(b[0], b[1], b[2], (int)p);
+  xr[p] = make_float4(fr[0], fr[1], fr[2], cf[p].w);
+  cr[p] = make_int4(b[0], b[1], b[2], (int)p);  // p: storage position
   unsigned kk = bin_index<D>(bm, b[0], b[1], b[2]);
   key[p] = kk;
   rank[p] = atomicAdd(&cnt[kk], 1u);
@@ -175,7 +176,7 @@ __global__ void k_bin_scatter(const unsigned* __restrict__ key, const unsigned* 
   cs[sl] = cr[p];
 }
 
-// Deterministic mode: order every bin by particle id so that every sum over a
+// Deterministic mode: order every bin by storage position so that every sum over a
 // bin runs in a fixed order.
 __global__ void k_bin_sort(const unsigned* __restrict__ key, const unsigned* __restrict__ rank,
                            const unsigned* __restrict__ start, long long np,
@@ -334,16 +335,13 @@ __device__ __forceinline__ bool lattice_coord(int& x, int n, int periodic) {
   return true;
 }
 
-// Post-stream moments at lattice cell (x, y, z), pulled from the stored f*:
-// sum of the stored values (rho - S) and the first moment j, in type R.
+// The stored values that stream into lattice cell (x, y, z): f*(x - e_a, a), or
+// f*(x, opp a) (halfway bounce-back) where x - e_a lies beyond a wall.
 template <int Q, class St>
-__device__ __forceinline__ void pull_moments(const typename St::T* __restrict__ f,
-                                             const Geometry& g, int x, int y, int z,
-                                             typename St::R& r, typename St::R (&j)[3]) {
+__device__ __forceinline__ void pull_load(const typename St::T* __restrict__ f, const Geometry& g,
+                                          int x, int y, int z, typename St::T (&v)[Q]) {
   using L = Lattice<Q>;
-  using R = typename St::R;
   const long long c = x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
-  R s = R(0), m0 = R(0), m1 = R(0), m2 = R(0);
 #pragma unroll
   for (int a = 0; a < Q; ++a) {
     int s0 = x - L::e(a, 0), s1 = y - L::e(a, 1), s2 = z - L::e(a, 2);
@@ -360,12 +358,26 @@ __device__ __forceinline__ void pull_moments(const typename St::T* __restrict__ 
       if (s2 < 0) { if (g.periodic[2]) s2 += g.n[2]; else bb = true; }
       else if (s2 >= g.n[2]) { if (g.periodic[2]) s2 -= g.n[2]; else bb = true; }
     }
-    long long src = s0 + (long long)g.n[0] * (s1 + (long long)g.n[1] * s2);
-    R v = St::load(bb ? f[opp(a) * g.pitch + c] : f[a * g.pitch + src]);
-    s += v;
-    if (L::e(a, 0)) m0 += L::e(a, 0) * v;
-    if (L::e(a, 1)) m1 += L::e(a, 1) * v;
-    if (L::e(a, 2)) m2 += L::e(a, 2) * v;
+    const long long src = s0 + (long long)g.n[0] * (s1 + (long long)g.n[1] * s2);
+    v[a] = bb ? f[opp(a) * g.pitch + c] : f[a * g.pitch + src];
+  }
+}
+
+// Zeroth and first moments of pulled values: sum of the stored values (rho - S)
+// and j, in type R.
+template <int Q, class St>
+__device__ __forceinline__ void sum_moments(const typename St::T (&v)[Q], typename St::R& r,
+                                            typename St::R (&j)[3]) {
+  using L = Lattice<Q>;
+  using R = typename St::R;
+  R s = R(0), m0 = R(0), m1 = R(0), m2 = R(0);
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    const R x = St::load(v[a]);
+    s += x;
+    if (L::e(a, 0)) m0 += L::e(a, 0) * x;
+    if (L::e(a, 1)) m1 += L::e(a, 1) * x;
+    if (L::e(a, 2)) m2 += L::e(a, 2) * x;
   }
   r = s;
   j[0] = m0;
@@ -387,38 +399,71 @@ struct CoupleArgs {
   Physics ph;
   BinMap bm;
   long long np;
-  const double* X;   // [d][np], step n
+  const double* X;   // [d][np], step n, by storage position
   const double* U;
-  double* Xn;        // [d][np], step n + 1
+  double* Xn;        // [d][np], step n + 1, by slot (also the sub-step state)
   double* Un;
+  // per-particle constants of step n by storage position, and their copies for
+  // step n + 1 by slot (written by the coupled kernel)
   const double* rad;
   const double* mass;
   const double* Ap;
   const double* buoy;
-  const double* gw;     // wall damping coefficient per particle
-  const float* radf;    // radius (FP32)
+  const double* gw;     // wall damping coefficient per particle (linear law)
+  const float4* cf;     // FP32 {mass, A_p, buoy, radius}
+  const unsigned* pid;  // user index
+  double* radn;
+  double* massn;
+  double* Apn;
+  double* buoyn;
+  double* gwn;
+  float4* cfn;
+  unsigned* pidn;
   const float4* xs;     // [np] FP32 in-cell position and radius of step n, sorted order
-  const int4* cs;       // [np] cell (x, y, z) and particle id, sorted order
+  const int4* cs;       // [np] cell (x, y, z) and storage position, sorted order
   float xf_margin;      // bound on the FP32 rounding error of a distance
-  double* gout;      // [d][np]
-  double* Fcout;     // [d][np]
+  double* gout;      // [d][np] by slot
+  double* Fcout;     // [d][np] by slot
+  double* rl;        // sub-cycling: [np] rho_l by slot
+  double* jl;        // sub-cycling: [d][np] j_l by slot
+  double* Fs;        // sub-cycling: [d][np] contact force of the sub-step by slot
   const unsigned* perm;
   const unsigned* start;
   const void* f;     // stored populations f*
   const void* mom;   // moment field (k_moments)
   void* F;           // force field
   unsigned* err;
-  int spread;        // 1: spread A_p g into F (through the tile's shared-memory copy)
+  int spread;        // 1: spread A_p g into F with atomics (0: ordered gather kernel)
 };
 
-// Contact forces (linear spring-dashpot, normal only) on the step-n state, one
-// thread per particle in sorted order: the 3^d neighbouring cells through the
-// cell list, then the walls. gamma = 2 beta sqrt(m_eff kn) with
-// beta = -ln e / sqrt(pi^2 + ln^2 e) fixes the restitution coefficient e.
-// Candidates are first screened in FP32 with a margin larger than the FP32
-// rounding of the positions (xf_margin), so only pairs that may overlap reach
-// the FP64 overlap test; the force itself is FP64.
-template <int D>
+// Magnitude of the normal contact force (positive = repulsive) for an overlap
+// delta > 0 and normal relative velocity vn (positive = separating), reduced
+// mass meff. Linear: k_n delta - gamma vn with gamma = 2 beta sqrt(meff k_n).
+// Hertz (Eq. 15): (4/3) E* sqrt(R*) delta^{3/2} - gamma vn with the
+// Hertz-Mindlin damping gamma = 2 sqrt(5/6) beta sqrt(S_n meff),
+// S_n = 2 E* sqrt(R* delta).
+template <bool HZ>
+__device__ __forceinline__ double normal_force(const Physics& ph, double delta, double vn,
+                                               double meff, double Rs, double Es) {
+  if constexpr (HZ) {
+    const double sd = sqrt(delta), sR = sqrt(Rs);
+    const double gam = ph.hz_damp * sqrt(2.0 * Es * sR * sd * meff);
+    return (4.0 / 3.0) * Es * sR * delta * sd - gam * vn;
+  }
+  const double gam = 2.0 * ph.beta * sqrt(meff * ph.kn);
+  return ph.kn * delta - gam * vn;
+}
+
+// Contact forces (normal only, linear spring-dashpot or Hertz) on the step-n
+// state (SUB = false) or on the sub-step state (SUB = true: positions and
+// velocities by slot in Xn, Un), one thread per particle in sorted order,
+// written by slot: the 3^d neighbouring cells through the cell list of the step
+// start, then the walls. beta = -ln e / sqrt(pi^2 + ln^2 e) fixes the
+// restitution coefficient e. Candidates are first screened in FP32 with a
+// margin larger than the FP32 rounding of the positions (xf_margin), plus twice
+// the largest sub-step displacement, so only pairs that may overlap reach the
+// FP64 overlap test; the force itself is FP64. HZ selects the Hertz law.
+template <int D, bool SUB, bool HZ>
 __global__ void __launch_bounds__(256) k_contacts(CoupleArgs A) {
   const long long sl = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (sl >= A.np) return;
@@ -431,7 +476,11 @@ __global__ void __launch_bounds__(256) k_contacts(CoupleArgs A) {
     atomicOr(A.err, ERR_INDEX);
     return;
   }
-  const float mrg = A.xf_margin;
+  // positions and velocities: step n by storage position, or the sub-step state by slot
+  auto Xat = [&](int k, unsigned i) { return SUB ? A.Xn[k * np + i] : A.X[k * np + i]; };
+  auto Uat = [&](int k, unsigned i) { return SUB ? A.Un[k * np + i] : A.U[k * np + i]; };
+  const unsigned me_i = SUB ? (unsigned)sl : p;
+  const float mrg = A.xf_margin + (SUB ? 2.f * (float)A.ph.skin : 0.f);
   const float4 me = A.xs[sl];
   const float xp[3] = {me.x, me.y, me.z};
   const float rpf = me.w;
@@ -445,25 +494,23 @@ __global__ void __launch_bounds__(256) k_contacts(CoupleArgs A) {
     for (int oy = -1; oy <= 1; ++oy) {
       int cy = bc[1] + oy;
       if (!lattice_coord(cy, g.n[1], g.periodic[1])) continue;
-      // the cells x-1, x, x+1 of this row, as runs of consecutive bins
-      unsigned runs[3][2];
-      int nrun = 0;
+      // the cells x-1, x, x+1 of this row: one run of consecutive bins in the
+      // common case, else each in-domain cell on its own
+      unsigned b[3];
+      bool ok[3];
 #pragma unroll
-      for (int ox = -1; ox <= 1; ++ox) {
-        int cx = bc[0] + ox;
-        if (!lattice_coord(cx, g.n[0], g.periodic[0])) continue;
-        const unsigned b = bin_index<D>(bm, cx, cy, cz);
-        if (nrun > 0 && runs[nrun - 1][1] == b) {
-          runs[nrun - 1][1] = b + 1;
-        } else {
-          runs[nrun][0] = b;
-          runs[nrun][1] = b + 1;
-          ++nrun;
-        }
+      for (int i = 0; i < 3; ++i) {
+        int cx = bc[0] + i - 1;
+        ok[i] = lattice_coord(cx, g.n[0], g.periodic[0]);
+        b[i] = ok[i] ? bin_index<D>(bm, cx, cy, cz) : 0u;
       }
+      const bool one = ok[0] && ok[1] && ok[2] && b[1] == b[0] + 1 && b[2] == b[1] + 1;
 #pragma unroll 1
-      for (int r = 0; r < nrun; ++r) {
-        const unsigned lo = A.start[runs[r][0]], hi = A.start[runs[r][1]];
+      for (int r = 0; r < (one ? 1 : 3); ++r) {
+        const bool okr = one || (r == 0 ? ok[0] : (r == 1 ? ok[1] : ok[2]));
+        if (!okr) continue;
+        const unsigned br = r == 0 ? b[0] : (r == 1 ? b[1] : b[2]);
+        const unsigned lo = A.start[br], hi = A.start[one ? b[2] + 1 : br + 1];
         if (hi > (unsigned)np || lo > hi) {
           atomicOr(A.err, ERR_INDEX);
           continue;
@@ -494,24 +541,25 @@ __global__ void __launch_bounds__(256) k_contacts(CoupleArgs A) {
             atomicOr(A.err, ERR_INDEX);
             continue;
           }
-          double X[3], s[3], d2 = 0.0;
+          const unsigned ot_i = SUB ? s2 : q;
+          double s[3], d2 = 0.0;
 #pragma unroll
           for (int k = 0; k < D; ++k) {
-            X[k] = A.X[k * np + p];
-            s[k] = min_image(X[k] - A.X[k * np + q], g.n[k], g.periodic[k]);
+            s[k] = min_image(Xat(k, me_i) - Xat(k, ot_i), g.n[k], g.periodic[k]);
             d2 += s[k] * s[k];
           }
           const double dist = sqrt(d2);
-          const double delta = A.rad[p] + A.rad[q] - dist;
+          const double rp = A.rad[p], rq = A.rad[q];
+          const double delta = rp + rq - dist;
           if (!(delta > 0.0) || !(dist > 0.0)) continue;
-          const double mi = A.mass[p], mq = A.mass[q];
-          const double meff = mi * mq / (mi + mq);
-          const double gam = 2.0 * A.ph.beta * sqrt(meff * A.ph.kn);
+          const double mp = A.mass[p], mq = A.mass[q];
+          const double meff = mp * mq / (mp + mq);
           const double inv = 1.0 / dist;
           double vn = 0.0;
 #pragma unroll
-          for (int k = 0; k < D; ++k) vn += (A.U[k * np + p] - A.U[k * np + q]) * (s[k] * inv);
-          const double mag = A.ph.kn * delta - gam * vn;
+          for (int k = 0; k < D; ++k) vn += (Uat(k, me_i) - Uat(k, ot_i)) * (s[k] * inv);
+          const double mag = normal_force<HZ>(A.ph, delta, vn, meff, HZ ? rp * rq / (rp + rq) : 0.0,
+                                              A.ph.Epp);
 #pragma unroll
           for (int k = 0; k < D; ++k) Fc[k] += mag * (s[k] * inv);
         }
@@ -523,194 +571,259 @@ __global__ void __launch_bounds__(256) k_contacts(CoupleArgs A) {
     if (g.periodic[k]) continue;
     const float nk = (float)g.n[k];
     const float xabs = (float)bc[k] + xp[k];
+    // walls are bodies at rest: m_eff = m, R* = R, the wall's E in E*
     if (xabs < rpf + mrg) {  // near the wall at 0 (normal +e_k)
-      const double delta = A.rad[p] - A.X[k * np + p];
-      if (delta > 0.0) Fc[k] += A.ph.kn * delta - A.gw[p] * A.U[k * np + p];
+      const double delta = A.rad[p] - Xat(k, me_i);
+      if (delta > 0.0) {
+        const double vn = Uat(k, me_i);
+        Fc[k] += HZ ? normal_force<true>(A.ph, delta, vn, A.mass[p], A.rad[p], A.ph.Epw)
+                    : A.ph.kn * delta - A.gw[p] * vn;
+      }
     }
     if (xabs > nk - rpf - mrg) {  // near the wall at n (normal -e_k)
-      const double delta = A.rad[p] - ((double)g.n[k] - A.X[k * np + p]);
-      if (delta > 0.0) Fc[k] -= A.ph.kn * delta + A.gw[p] * A.U[k * np + p];
+      const double delta = A.rad[p] - ((double)g.n[k] - Xat(k, me_i));
+      if (delta > 0.0) {
+        const double vn = -Uat(k, me_i);
+        Fc[k] -= HZ ? normal_force<true>(A.ph, delta, vn, A.mass[p], A.rad[p], A.ph.Epw)
+                    : A.ph.kn * delta - A.gw[p] * vn;
+      }
     }
   }
 #pragma unroll
-  for (int k = 0; k < D; ++k) A.Fcout[k * np + p] = Fc[k];
+  for (int k = 0; k < D; ++k) (SUB ? A.Fs : A.Fcout)[k * np + sl] = Fc[k];
 }
 
-// Post-stream moments of every cell of the tiles that hold particles or touch
-// a tile that does (the 2-cell delta stencil never reaches further), one CTA per
-// tile of TileDims cells: mom[0] = sum of stored values (rho - S), mom[1..d] = j.
-// Cells of other tiles are left untouched; no stencil reads them.
+// Shape of the moment kernel: cells per thread (as many loads in flight as the
+// registers allow) and tiles per CTA of 256 threads.
 template <int Q, class St>
-__global__ void __launch_bounds__(256) k_moments(Geometry g, BinMap bm,
+struct MomentsShape {
+  static constexpr int D = Lattice<Q>::D;
+  static constexpr int TC = TileDims<D>::TC;
+  static constexpr int CPT = (D == 3 || sizeof(typename St::T) == 8) ? 2 : 4;
+  static constexpr int MINB = sizeof(typename St::T) == 8 ? 2 : 4;  // CTAs per SM
+  static constexpr int KT = CPT * 256 / TC;
+};
+
+// Post-stream moments of every cell of the tiles that hold particles or touch
+// a tile that does (the 2-cell delta stencil never reaches further), KT tiles of
+// TileDims cells per CTA: mom[0] = sum of stored values (rho - S), mom[1..d] = j.
+// Each thread issues the loads of all its cells before it sums any of them.
+// A cell whose neighbours all lie inside the lattice (no wall, no wrap) reads
+// its sources at fixed 32-bit offsets; only cells on the lattice faces take the
+// general path. Cells of other tiles are left untouched; no stencil reads them.
+template <int Q, class St>
+__global__ void __launch_bounds__(256, MomentsShape<Q, St>::MINB) k_moments(Geometry g, BinMap bm,
                                                  const unsigned* __restrict__ start,
                                                  const typename St::T* __restrict__ f,
                                                  typename St::R* __restrict__ mom) {
+  using Sh = MomentsShape<Q, St>;
   using L = Lattice<Q>;
+  using T = typename St::T;
   using R = typename St::R;
-  constexpr int D = L::D;
+  constexpr int D = Sh::D;
+  constexpr int NB = D == 3 ? 27 : 9;
   using TD = TileDims<D>;
-  const int tile = blockIdx.x;
-  const int t[3] = {tile % bm.nt[0], (tile / bm.nt[0]) % bm.nt[1], tile / (bm.nt[0] * bm.nt[1])};
-  int busy = 0;
-  if (threadIdx.x < (D == 3 ? 27 : 9)) {
-    const int o[3] = {(int)threadIdx.x % 3 - 1, ((int)threadIdx.x / 3) % 3 - 1,
-                      D == 3 ? (int)threadIdx.x / 9 - 1 : 0};
-    int nb[3];
-    bool ok = true;
+  __shared__ int busy[Sh::KT];
+  __shared__ int corner[Sh::KT][3];  // first cell of each tile
+  const int ntiles = bm.nt[0] * bm.nt[1] * bm.nt[2];
+  const int tile0 = blockIdx.x * Sh::KT;
+  if (threadIdx.x < Sh::KT) {
+    const int tile = tile0 + threadIdx.x;
+    const int r = tile / bm.nt[0];
+    busy[threadIdx.x] = 0;
+    corner[threadIdx.x][0] = (tile - r * bm.nt[0]) * TD::TX;
+    corner[threadIdx.x][1] = (r % bm.nt[1]) * TD::TY;
+    corner[threadIdx.x][2] = (r / bm.nt[1]) * TD::TZ;
+  }
+  __syncthreads();
+  if (threadIdx.x < Sh::KT * NB) {
+    const int k = threadIdx.x / NB, o = threadIdx.x % NB;
+    if (tile0 + k < ntiles) {
+      const int t[3] = {corner[k][0] / TD::TX, corner[k][1] / TD::TY, corner[k][2] / TD::TZ};
+      const int off[3] = {o % 3 - 1, (o / 3) % 3 - 1, D == 3 ? o / 9 - 1 : 0};
+      int nb[3];
+      bool ok = true;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      nb[k] = t[k] + o[k];
-      if (nb[k] < 0 || nb[k] >= bm.nt[k]) {
-        if (g.periodic[k]) nb[k] = (nb[k] + bm.nt[k]) % bm.nt[k];
-        else ok = false;
+      for (int a = 0; a < 3; ++a) {
+        nb[a] = t[a] + off[a];
+        if (nb[a] < 0 || nb[a] >= bm.nt[a]) {
+          if (g.periodic[a]) nb[a] = (nb[a] + bm.nt[a]) % bm.nt[a];
+          else ok = false;
+        }
+      }
+      if (ok) {
+        const unsigned nt = (unsigned)(nb[0] + bm.nt[0] * (nb[1] + bm.nt[1] * nb[2]));
+        if (start[(nt + 1) * (unsigned)TD::TC] != start[nt * (unsigned)TD::TC]) busy[k] = 1;
       }
     }
-    if (ok) {
-      const unsigned nt = (unsigned)(nb[0] + bm.nt[0] * (nb[1] + bm.nt[1] * nb[2]));
-      busy = start[(nt + 1) * (unsigned)TD::TC] != start[nt * (unsigned)TD::TC];
+  }
+  __syncthreads();
+  const int n0 = g.n[0], n01 = g.n[0] * g.n[1];
+  T v[Sh::CPT][Q];
+  int cell[Sh::CPT];
+  bool on[Sh::CPT];
+#pragma unroll
+  for (int c = 0; c < Sh::CPT; ++c) {
+    const int lin = c * 256 + (int)threadIdx.x;
+    const int k = lin / TD::TC, i = lin % TD::TC;
+    const int x = corner[k][0] + i % TD::TX;
+    const int y = corner[k][1] + (i / TD::TX) % TD::TY;
+    const int z = corner[k][2] + i / (TD::TX * TD::TY);
+    on[c] = tile0 + k < ntiles && busy[k] && x < g.n[0] && y < g.n[1] && z < g.n[2];
+    cell[c] = x + n0 * y + n01 * z;
+    if (!on[c]) continue;
+    const bool inner = x >= 1 && x <= g.n[0] - 2 && y >= 1 && y <= g.n[1] - 2 &&
+                       (D == 2 || (z >= 1 && z <= g.n[2] - 2));
+    if (inner) {
+      const T* fa = f;
+#pragma unroll
+      for (int a = 0; a < Q; ++a) {
+        v[c][a] = fa[cell[c] - (L::e(a, 0) + n0 * L::e(a, 1) + n01 * L::e(a, 2))];
+        fa += g.pitch;
+      }
+    } else {
+      pull_load<Q, St>(f, g, x, y, z, v[c]);
     }
   }
-  if (!__syncthreads_or(busy)) return;
-  for (int i = threadIdx.x; i < TD::TC; i += blockDim.x) {
-    const int x = t[0] * TD::TX + i % TD::TX;
-    const int y = t[1] * TD::TY + (i / TD::TX) % TD::TY;
-    const int z = t[2] * TD::TZ + i / (TD::TX * TD::TY);
-    if (x >= g.n[0] || y >= g.n[1] || z >= g.n[2]) continue;
+#pragma unroll
+  for (int c = 0; c < Sh::CPT; ++c) {
+    if (!on[c]) continue;
     R r, j[3];
-    pull_moments<Q, St>(f, g, x, y, z, r, j);
-    const long long c = x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
-    store_moments<R>(mom, c, r, j);
+    sum_moments<Q, St>(v[c], r, j);
+    store_moments<R>(mom, cell[c], r, j);
   }
 }
 
-// Particle coupling, one thread per particle in cell-sorted order: interpolate
-// rho, j from the moment field with the delta weights (Eq. 4), take the contact
-// force (k_contacts), advance U and X (Eq. 13), form g = 2 (rho_l U - j_l)
-// (Eqs. 6-7) and spread A_p g w into F (Eq. 9).
-// Spreading adds each tap with one vector atomic per cell (FP32) or one atomic
-// per component (FP64); the cell-sorted order keeps a warp's taps close together.
-template <int Q, int W, class St, typename FT>
-__global__ void __launch_bounds__(256) k_couple(CoupleArgs A) {
-  using L = Lattice<Q>;
-  using R = typename St::R;
-  constexpr int D = L::D;
-  constexpr int WZ = D == 3 ? W : 1;
-  const long long sl = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+// ---------------------------------------------------------------------------
+// Interpolation (Eq. 4 with the spreading kernel, or Eq. 5) and spreading
+// (Eq. 9) of one particle
+// ---------------------------------------------------------------------------
+// Cubic Lagrange basis on the nodes 0, 1, 2, 3 at coordinate t (Eq. 5 with
+// unit node spacing): w_i = prod_{l != i} (t - l) / (i - l).
+template <typename WT>
+__device__ __forceinline__ void lagrange_weights(WT t, WT (&w)[4]) {
+  const WT t1 = t - WT(1), t2 = t - WT(2), t3 = t - WT(3);
+  const WT sixth = WT(1) / WT(6);
+  w[0] = -(t1 * t2 * t3) * sixth;
+  w[1] = WT(0.5) * (t * t2 * t3);
+  w[2] = -WT(0.5) * (t * t1 * t3);
+  w[3] = (t * t1 * t2) * sixth;
+}
+
+// The 4-node block of Eq. (5) along one axis: first = floor(X - 1/2) - 1,
+// shifted into [0, n - 4] on a wall axis (one-sided next to the wall), wrapped
+// on a periodic axis; t = X - (first + 1/2).
+template <typename WT>
+__device__ __forceinline__ void lagrange_block(int first, int n, int periodic, Taps<4, WT>& t) {
+  t.first = first;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int k = first + i;
+    if (periodic) {
+      k %= n;
+      if (k < 0) k += n;
+    }
+    t.idx[i] = k;
+  }
+}
+
+template <typename WT>
+__device__ __forceinline__ void axis_lagrange(double X, int n, int periodic, Taps<4, WT>& t) {
+  int first = (int)floor(X - 0.5) - 1;
+  if (!periodic) first = first < 0 ? 0 : (first > n - 4 ? n - 4 : first);
+  lagrange_block<WT>(first, n, periodic, t);
+  lagrange_weights<WT>((WT)(X - ((double)first + 0.5)), t.w);
+}
+
+// The same from the cell c and the FP32 offset f inside it (X = c + f).
+__device__ __forceinline__ void axis_lagrange_local(int c, float f, int n, int periodic,
+                                                    Taps<4, float>& t) {
+  int first = c + (int)floorf(f - 0.5f) - 1;
+  if (!periodic) first = first < 0 ? 0 : (first > n - 4 ? n - 4 : first);
+  lagrange_block<float>(first, n, periodic, t);
+  lagrange_weights<float>((float)(c - first) - 0.5f + f, t.w);
+}
+
+// Per-axis taps of one particle: LAG selects Eq. (5) (WI = 4), else the delta
+// kernel of width WI. FP32 modes work from the cell and in-cell offset, FP64
+// from the FP64 position.
+template <int D, int WI, bool LAG, typename R>
+__device__ __forceinline__ void particle_taps(const Geometry& g, const int4& mc, const float4& mf,
+                                              const double (&X)[3], Taps<WI, R>& tx,
+                                              Taps<WI, R>& ty, Taps<WI, R>& tz) {
+  static_assert(!LAG || WI == 4, "the Lagrange block has four nodes");
+  if constexpr (sizeof(R) == 4) {
+    if constexpr (LAG) {
+      axis_lagrange_local(mc.x, mf.x, g.n[0], g.periodic[0], tx);
+      axis_lagrange_local(mc.y, mf.y, g.n[1], g.periodic[1], ty);
+      if constexpr (D == 3) axis_lagrange_local(mc.z, mf.z, g.n[2], g.periodic[2], tz);
+    } else {
+      axis_taps_local<WI>(mc.x, mf.x, g.n[0], g.periodic[0], tx);
+      axis_taps_local<WI>(mc.y, mf.y, g.n[1], g.periodic[1], ty);
+      if constexpr (D == 3) axis_taps_local<WI>(mc.z, mf.z, g.n[2], g.periodic[2], tz);
+    }
+  } else {
+    if constexpr (LAG) {
+      axis_lagrange<R>(X[0], g.n[0], g.periodic[0], tx);
+      axis_lagrange<R>(X[1], g.n[1], g.periodic[1], ty);
+      if constexpr (D == 3) axis_lagrange<R>(X[2], g.n[2], g.periodic[2], tz);
+    } else {
+      axis_taps<WI, R>(X[0], g.n[0], g.periodic[0], tx);
+      axis_taps<WI, R>(X[1], g.n[1], g.periodic[1], ty);
+      if constexpr (D == 3) axis_taps<WI, R>(X[2], g.n[2], g.periodic[2], tz);
+    }
+  }
+}
+
+// Eq. (4) on the moments: rs = sum w (rho - S), js = sum w j over the taps.
+template <int D, int WI, typename R>
+__device__ __forceinline__ void gather_moments(const CoupleArgs& A, const Taps<WI, R>& tx,
+                                               const Taps<WI, R>& ty, const Taps<WI, R>& tz,
+                                               R& rs, R (&js)[3]) {
+  constexpr int WZ = D == 3 ? WI : 1;
   const Geometry& g = A.g;
-  const long long np = A.np;
-  Taps<W, R> tx, ty, tz;
-  FT amp[3] = {FT(0), FT(0), FT(0)};
-  bool act = sl < A.np;
-  unsigned p = 0;
-  int4 mc = make_int4(0, 0, 0, 0);
-  float4 mf = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (act) {
-    mc = A.cs[sl];
-    mf = A.xs[sl];
-    p = (unsigned)mc.w;
-    if (p >= (unsigned)np) {
-      atomicOr(A.err, ERR_INDEX);
-      act = false;
-    }
-  }
-  if (act) {
-    double X[3] = {0.0, 0.0, 0.0}, U[3] = {0.0, 0.0, 0.0}, Fc[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      X[k] = A.X[k * np + p];
-      U[k] = A.U[k * np + p];
-      Fc[k] = A.Fcout[k * np + p];
-    }
-    const double mi = A.mass[p], Ap = A.Ap[p], bu = A.buoy[p];
-    const R* mom = (const R*)A.mom;
-
-    // --- interpolation of rho, j (Eq. 4) ---
-    if constexpr (sizeof(R) == 4) {
-      axis_taps_local<W>(mc.x, mf.x, g.n[0], g.periodic[0], tx);
-      axis_taps_local<W>(mc.y, mf.y, g.n[1], g.periodic[1], ty);
-      if constexpr (D == 3) axis_taps_local<W>(mc.z, mf.z, g.n[2], g.periodic[2], tz);
-    } else {
-      axis_taps<W, R>(X[0], g.n[0], g.periodic[0], tx);
-      axis_taps<W, R>(X[1], g.n[1], g.periodic[1], ty);
-      if constexpr (D == 3) axis_taps<W, R>(X[2], g.n[2], g.periodic[2], tz);
-    }
-    R rs = R(0), js[3] = {R(0), R(0), R(0)};
+  const R* mom = (const R*)A.mom;
+  rs = R(0);
+  js[0] = js[1] = js[2] = R(0);
 #pragma unroll 1
-    for (int iz = 0; iz < WZ; ++iz) {
-      R wz = R(1);
-      long long zoff = 0;
-      if constexpr (D == 3) {
-        wz = tz.w[iz];
-        zoff = (long long)tz.idx[iz] * g.n[1];
-      }
-      if (wz == R(0)) continue;
+  for (int iz = 0; iz < WZ; ++iz) {
+    R wz = R(1);
+    long long zoff = 0;
+    if constexpr (D == 3) {
+      wz = tz.w[iz];
+      zoff = (long long)tz.idx[iz] * g.n[1];
+    }
+    if (wz == R(0)) continue;
 #pragma unroll
-      for (int iy = 0; iy < W; ++iy) {
-        const R wyz = ty.w[iy] * wz;
-        const long long row = (zoff + ty.idx[iy]) * g.n[0];
+    for (int iy = 0; iy < WI; ++iy) {
+      const R wyz = ty.w[iy] * wz;
+      const long long row = (zoff + ty.idx[iy]) * g.n[0];
 #pragma unroll
-        for (int ix = 0; ix < W; ++ix) {
-          const R wt = tx.w[ix] * wyz;
-          if (wt == R(0)) continue;
-          R m[4];
-          if (row + tx.idx[ix] < 0 || row + tx.idx[ix] >= g.ncell) {
-            atomicOr(A.err, ERR_INDEX);
-            continue;
-          }
-          load_moments<R>(mom, row + tx.idx[ix], m);
-          rs += wt * m[0];
-#pragma unroll
-          for (int k = 0; k < D; ++k) js[k] += wt * m[k + 1];
+      for (int ix = 0; ix < WI; ++ix) {
+        const R wt = tx.w[ix] * wyz;
+        if (wt == R(0)) continue;
+        if (row + tx.idx[ix] < 0 || row + tx.idx[ix] >= g.ncell) {
+          atomicOr(A.err, ERR_INDEX);
+          continue;
         }
+        R m[4];
+        load_moments<R>(mom, row + tx.idx[ix], m);
+        rs += wt * m[0];
+#pragma unroll
+        for (int k = 0; k < D; ++k) js[k] += wt * m[k + 1];
       }
     }
-    const double rho_l = (double)St::S + (double)rs;
-    double j_l[3] = {(double)js[0], (double)js[1], (double)js[2]};
-
-    // --- particle update (Eq. 13) and force density (Eqs. 6-7) ---
-    double Un[3], Ub[3], gg[3];
-    if (A.ph.implicit_drag) {
-      const double inv = rcp_newton<sizeof(R) == 4 ? 1 : 2>(mi + 2.0 * Ap * rho_l);
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        Un[k] = (mi * U[k] + 2.0 * Ap * j_l[k] + bu * A.ph.gravity[k] + Fc[k]) * inv;
-        Ub[k] = Un[k];
-      }
-    } else {
-      const double invm = 1.0 / mi;
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        Un[k] = U[k] + (bu * A.ph.gravity[k] + Fc[k] - Ap * 2.0 * (rho_l * U[k] - j_l[k])) * invm;
-        Ub[k] = U[k];
-      }
-    }
-    bool bad = false, esc = false;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      gg[k] = 2.0 * (rho_l * Ub[k] - j_l[k]);
-      if constexpr (sizeof(FT) == 4) amp[k] = (float)gg[k] * (float)Ap;
-      else amp[k] = (FT)(Ap * gg[k]);
-      double xn = X[k] + Un[k];
-      if (g.periodic[k]) {
-        const double N = (double)g.n[k];
-        if (xn < 0.0) xn += N;
-        else if (xn >= N) xn -= N;
-        if (!(xn >= 0.0 && xn < N)) xn = xn - N * floor(xn / N);  // |U| > N: not physical
-        if (!(xn >= 0.0 && xn < N)) xn = 0.0;
-      } else if (outside_bits(xn, (double)g.n[k])) {
-        esc = true;
-      }
-      bad |= not_finite_bits(xn) || not_finite_bits(Un[k]);
-      A.Xn[k * np + p] = xn;
-      A.Un[k * np + p] = Un[k];
-      A.gout[k * np + p] = gg[k];
-    }
-    if (bad) atomicOr(A.err, ERR_PARTICLE_NONFINITE);
-    if (esc) atomicOr(A.err, ERR_ESCAPED);
   }
+}
 
-  // --- spreading (Eq. 9) ---
-  if (!A.spread || !act) return;
+// Eq. (9): add amp * w to F at every tap (one vector atomic per cell in FP32,
+// one atomic per component in FP64).
+template <int D, int W, typename TW, typename FT>
+__device__ __forceinline__ void spread_amp(const CoupleArgs& A, const Taps<W, TW>& tx,
+                                           const Taps<W, TW>& ty, const Taps<W, TW>& tz,
+                                           const FT (&amp)[3]) {
+  constexpr int WZ = D == 3 ? W : 1;
+  const Geometry& g = A.g;
   FT* F = (FT*)A.F;
 #pragma unroll 1
   for (int iz = 0; iz < WZ; ++iz) {
@@ -736,9 +849,277 @@ __global__ void __launch_bounds__(256) k_couple(CoupleArgs A) {
   }
 }
 
+// Position update along one axis: periodic axes wrap, wall axes report a
+// particle outside [0, n].
+__device__ __forceinline__ double advance_axis(double x, int n, int periodic, bool& esc) {
+  if (periodic) {
+    const double N = (double)n;
+    if (x < 0.0) x += N;
+    else if (x >= N) x -= N;
+    if (!(x >= 0.0 && x < N)) x = x - N * floor(x / N);  // |U| > N: not physical
+    if (!(x >= 0.0 && x < N)) x = 0.0;
+  } else if (outside_bits(x, (double)n)) {
+    esc = true;
+  }
+  return x;
+}
+
+// The particle's constants move with it to its slot.
+__device__ __forceinline__ void move_constants(const CoupleArgs& A, unsigned p, long long sl) {
+  A.radn[sl] = A.rad[p];
+  A.massn[sl] = A.mass[p];
+  A.Apn[sl] = A.Ap[p];
+  A.buoyn[sl] = A.buoy[p];
+  A.gwn[sl] = A.gw[p];
+  A.cfn[sl] = A.cf[p];
+  A.pidn[sl] = A.pid[p];
+}
+
+// Particle coupling, one thread per particle in cell-sorted order: interpolate
+// rho, j from the moment field (Eq. 4; the delta kernel, or Eq. 5 when LAG),
+// take the contact force (k_contacts), advance U and X (Eq. 13), form
+// g = 2 (rho_l U_b - j_l) (Eqs. 6-7) and spread A_p g w into F (Eq. 9) with the
+// delta kernel of width W. The new state, g and the particle's constants are
+// written at its slot, which becomes its storage position for the next step.
+// FP64 mode solves the update in FP64. The FP32-storage modes (whose rho_l, j_l
+// come from FP32 moments) form the velocity increment U' - U and g in FP32 and
+// add the increment to the FP64 state: positions and velocities stay FP64.
+template <int Q, int W, class St, typename FT, bool LAG>
+__global__ void __launch_bounds__(256, (Lattice<Q>::D == 2 && sizeof(typename St::R) == 4) ? 5 : 1)
+    k_couple(CoupleArgs A) {
+  using L = Lattice<Q>;
+  using R = typename St::R;
+  constexpr int D = L::D;
+  constexpr int WI = LAG ? 4 : W;
+  const long long sl = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const Geometry& g = A.g;
+  const long long np = A.np;
+  Taps<WI, R> tx, ty, tz;
+  FT amp[3] = {FT(0), FT(0), FT(0)};
+  bool act = sl < A.np;
+  unsigned p = 0;
+  int4 mc = make_int4(0, 0, 0, 0);
+  float4 mf = make_float4(0.f, 0.f, 0.f, 0.f);
+  double X[3] = {0.0, 0.0, 0.0};
+  if (act) {
+    mc = A.cs[sl];
+    mf = A.xs[sl];
+    p = (unsigned)mc.w;
+    if (p >= (unsigned)np) {
+      atomicOr(A.err, ERR_INDEX);
+      act = false;
+    }
+  }
+  if (act) {
+    double U[3] = {0.0, 0.0, 0.0}, Fc[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      X[k] = A.X[k * np + p];
+      U[k] = A.U[k * np + p];
+      Fc[k] = A.Fcout[k * np + sl];
+    }
+    // --- interpolation of rho, j (Eq. 4) ---
+    particle_taps<D, WI, LAG, R>(g, mc, mf, X, tx, ty, tz);
+    R rs, js[3];
+    gather_moments<D, WI, R>(A, tx, ty, tz, rs, js);
+
+    // --- particle update (Eq. 13) and force density (Eqs. 6-7) ---
+    double Un[3];
+    bool bad = false, esc = false;
+    if constexpr (sizeof(R) == 8) {
+      const double mi = A.mass[p], Ap = A.Ap[p], bu = A.buoy[p];
+      const double rho_l = (double)St::S + rs;
+      double Ub[3];
+      if (A.ph.implicit_drag) {
+        const double inv = rcp_newton<2>(mi + 2.0 * Ap * rho_l);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          Un[k] = (mi * U[k] + 2.0 * Ap * js[k] + bu * A.ph.gravity[k] + Fc[k]) * inv;
+          Ub[k] = Un[k];
+        }
+      } else {
+        const double invm = 1.0 / mi;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          Un[k] = U[k] + (bu * A.ph.gravity[k] + Fc[k] - Ap * 2.0 * (rho_l * U[k] - js[k])) * invm;
+          Ub[k] = U[k];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const double gg = 2.0 * (rho_l * Ub[k] - js[k]);
+        amp[k] = (FT)(Ap * gg);
+        A.gout[k * np + sl] = gg;
+      }
+    } else {
+      const float4 cc = A.cf[p];  // mass, A_p, buoy, radius
+      const float rho = (float)St::S + rs;
+      float Uf[3], dU[3], Ub[3];
+#pragma unroll
+      for (int k = 0; k < D; ++k) Uf[k] = (float)U[k];
+      if (A.ph.implicit_drag) {
+        // U' - U = (2 A_p (j_l - rho_l U) + buoy g + F_c) / (m + 2 A_p rho_l)
+        const float inv = 1.f / (cc.x + 2.f * cc.y * rho);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          dU[k] = (2.f * cc.y * (js[k] - rho * Uf[k]) + cc.z * A.ph.gravityf[k] + (float)Fc[k]) * inv;
+          Ub[k] = Uf[k] + dU[k];
+        }
+      } else {
+        const float invm = 1.f / cc.x;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          dU[k] = (cc.z * A.ph.gravityf[k] + (float)Fc[k] - 2.f * cc.y * (rho * Uf[k] - js[k])) * invm;
+          Ub[k] = Uf[k];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        Un[k] = U[k] + (double)dU[k];
+        const float gg = 2.f * (rho * Ub[k] - js[k]);
+        amp[k] = (FT)(gg * cc.y);
+        A.gout[k * np + sl] = (double)gg;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const double xn = advance_axis(X[k] + Un[k], g.n[k], g.periodic[k], esc);
+      bad |= not_finite_bits(xn) || not_finite_bits(Un[k]);
+      A.Xn[k * np + sl] = xn;
+      A.Un[k * np + sl] = Un[k];
+    }
+    if (bad) atomicOr(A.err, ERR_PARTICLE_NONFINITE);
+    if (esc) atomicOr(A.err, ERR_ESCAPED);
+    move_constants(A, p, sl);
+  }
+
+  // --- spreading (Eq. 9) with the delta kernel ---
+  if (!A.spread || !act) return;
+  if constexpr (LAG) {
+    Taps<W, R> sx, sy, sz;
+    particle_taps<D, W, false, R>(g, mc, mf, X, sx, sy, sz);
+    spread_amp<D, W, R, FT>(A, sx, sy, sz, amp);
+  } else {
+    spread_amp<D, W, R, FT>(A, tx, ty, tz, amp);
+  }
+}
+
+// DEM sub-cycling, step start: interpolate rho_l, j_l once (Eq. 4 / Eq. 5) and
+// store them by slot, copy the step-n state to the slot-ordered buffers Xn, Un
+// (the sub-step state), clear the accumulated force density and contact force,
+// and move the constants to their slots.
+template <int Q, int W, class St, bool LAG>
+__global__ void __launch_bounds__(256) k_sub_init(CoupleArgs A) {
+  using R = typename St::R;
+  constexpr int D = Lattice<Q>::D;
+  constexpr int WI = LAG ? 4 : W;
+  const long long sl = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (sl >= A.np) return;
+  const long long np = A.np;
+  const int4 mc = A.cs[sl];
+  const float4 mf = A.xs[sl];
+  const unsigned p = (unsigned)mc.w;
+  if (p >= (unsigned)np) {
+    atomicOr(A.err, ERR_INDEX);
+    return;
+  }
+  double X[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    X[k] = A.X[k * np + p];
+    A.Xn[k * np + sl] = X[k];
+    A.Un[k * np + sl] = A.U[k * np + p];
+    A.gout[k * np + sl] = 0.0;
+    A.Fcout[k * np + sl] = 0.0;
+  }
+  Taps<WI, R> tx, ty, tz;
+  particle_taps<D, WI, LAG, R>(A.g, mc, mf, X, tx, ty, tz);
+  R rs, js[3];
+  gather_moments<D, WI, R>(A, tx, ty, tz, rs, js);
+  A.rl[sl] = (double)St::S + (double)rs;
+#pragma unroll
+  for (int k = 0; k < D; ++k) A.jl[k * np + sl] = (double)js[k];
+  move_constants(A, p, sl);
+}
+
+// One DEM sub-step of length h = 1/S for every particle (by slot), FP64:
+//   implicit: U' = (m U + h (2 A_p j_l + buoy g + F_c)) / (m + 2 A_p rho_l h),
+//   explicit: U' = U + h (buoy g + F_c - 2 A_p (rho_l U - j_l)) / m,
+//   X' = X + h U';
+// g and F_c accumulate h 2 (rho_l U_b - j_l) and h F_c. A particle farther than
+// the skin from its step-start cell position raises ERR_SKIN: the cell list of
+// the step start would no longer hold all its contacts.
+template <int D>
+__global__ void __launch_bounds__(256) k_substep(CoupleArgs A, double h) {
+  const long long sl = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (sl >= A.np) return;
+  const long long np = A.np;
+  const Geometry& g = A.g;
+  const double m = A.massn[sl], Ap = A.Apn[sl], bu = A.buoyn[sl], rho = A.rl[sl];
+  const int4 mc = A.cs[sl];
+  const float4 mf = A.xs[sl];
+  const int c0[3] = {mc.x, mc.y, mc.z};
+  const float f0[3] = {mf.x, mf.y, mf.z};
+  bool bad = false, esc = false, far = false;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const double U = A.Un[k * np + sl], j = A.jl[k * np + sl], Fc = A.Fs[k * np + sl];
+    double Un, Ub;
+    if (A.ph.implicit_drag) {
+      Un = (m * U + h * (2.0 * Ap * j + bu * A.ph.gravity[k] + Fc)) / (m + 2.0 * Ap * rho * h);
+      Ub = Un;
+    } else {
+      Un = U + h * (bu * A.ph.gravity[k] + Fc - Ap * 2.0 * (rho * U - j)) / m;
+      Ub = U;
+    }
+    A.gout[k * np + sl] += h * 2.0 * (rho * Ub - j);
+    A.Fcout[k * np + sl] += h * Fc;
+    const double xn = advance_axis(A.Xn[k * np + sl] + h * Un, g.n[k], g.periodic[k], esc);
+    bad |= not_finite_bits(xn) || not_finite_bits(Un);
+    const double moved = min_image(xn - ((double)c0[k] + (double)f0[k]), g.n[k], g.periodic[k]);
+    far |= !(fabs(moved) <= A.ph.skin);
+    A.Xn[k * np + sl] = xn;
+    A.Un[k * np + sl] = Un;
+  }
+  if (bad) atomicOr(A.err, ERR_PARTICLE_NONFINITE);
+  if (esc) atomicOr(A.err, ERR_ESCAPED);
+  if (far) atomicOr(A.err, ERR_SKIN);
+}
+
+// DEM sub-cycling, step end: spread A_p times the sub-step average of g with the
+// delta kernel at the step-start position (Eq. 9), as in the single-step path.
+template <int Q, int W, class St, typename FT>
+__global__ void __launch_bounds__(256) k_sub_spread(CoupleArgs A) {
+  using R = typename St::R;
+  constexpr int D = Lattice<Q>::D;
+  const long long sl = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (sl >= A.np) return;
+  const long long np = A.np;
+  const int4 mc = A.cs[sl];
+  const float4 mf = A.xs[sl];
+  const unsigned p = (unsigned)mc.w;
+  if (p >= (unsigned)np) {
+    atomicOr(A.err, ERR_INDEX);
+    return;
+  }
+  double X[3] = {0.0, 0.0, 0.0};
+  if constexpr (sizeof(R) == 8) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) X[k] = A.X[k * np + p];
+  }
+  const double Ap = A.Apn[sl];
+  FT amp[3] = {FT(0), FT(0), FT(0)};
+#pragma unroll
+  for (int k = 0; k < D; ++k) amp[k] = (FT)(Ap * A.gout[k * np + sl]);
+  Taps<W, R> tx, ty, tz;
+  particle_taps<D, W, false, R>(A.g, mc, mf, X, tx, ty, tz);
+  spread_amp<D, W, R, FT>(A, tx, ty, tz, amp);
+}
+
 // Deterministic spreading: every cell gathers, in a fixed order (neighbour cells
-// by ascending z, y, x offset; particles by id inside a cell), the A_p g w of
-// every particle whose stencil covers it. Writes every cell of F.
+// by ascending z, y, x offset; particles by storage position inside a cell), the
+// A_p g w of every particle whose stencil covers it (X and A_p by storage
+// position, g by slot). Writes every cell of F.
 template <int D, int W, typename FT>
 __global__ void __launch_bounds__(256) k_spread_gather(Geometry g, BinMap bm, long long np,
                                                        const double* __restrict__ X,
@@ -784,7 +1165,7 @@ __global__ void __launch_bounds__(256) k_spread_gather(Geometry g, BinMap bm, lo
           if (wt == FT(0)) continue;
           const double a = Ap[p];
 #pragma unroll
-          for (int k = 0; k < D; ++k) acc[k] += (FT)(a * gin[k * np + p]) * wt;
+          for (int k = 0; k < D; ++k) acc[k] += (FT)(a * gin[k * np + sl]) * wt;
         }
       }
     }
@@ -793,22 +1174,36 @@ __global__ void __launch_bounds__(256) k_spread_gather(Geometry g, BinMap bm, lo
   store_force<D, FT>(F, c, acc);
 }
 
+// g and Fc of the last step are stored by that step's slot, which is the storage
+// position of the current state: Ap and pid of the current buffer match them.
 __global__ void k_forces(long long np, int d, const double* __restrict__ Ap,
                          const double* __restrict__ gin, const double* __restrict__ Fc,
-                         double* __restrict__ f_fpi, double* __restrict__ f_c) {
-  long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (p >= np) return;
+                         const unsigned* __restrict__ pid, double* __restrict__ f_fpi,
+                         double* __restrict__ f_c, unsigned* __restrict__ err) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  const unsigned p = pid[i];
+  if (p >= (unsigned long long)np) {
+    atomicOr(err, ERR_INDEX);
+    return;
+  }
   for (int k = 0; k < d; ++k) {
-    if (f_fpi) f_fpi[p * d + k] = -Ap[p] * gin[k * np + p];
-    if (f_c) f_c[p * d + k] = Fc[k * np + p];
+    if (f_fpi) f_fpi[(long long)p * d + k] = -Ap[i] * gin[k * np + i];
+    if (f_c) f_c[(long long)p * d + k] = Fc[k * np + i];
   }
 }
 
 __global__ void k_interleave(long long np, int d, const double* __restrict__ soa,
-                             double* __restrict__ aos) {
-  long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (p >= np) return;
-  for (int k = 0; k < d; ++k) aos[p * d + k] = soa[k * np + p];
+                             const unsigned* __restrict__ pid, double* __restrict__ aos,
+                             unsigned* __restrict__ err) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  const unsigned p = pid[i];
+  if (p >= (unsigned long long)np) {
+    atomicOr(err, ERR_INDEX);
+    return;
+  }
+  for (int k = 0; k < d; ++k) aos[(long long)p * d + k] = soa[k * np + i];
 }
 
 
@@ -848,23 +1243,27 @@ __global__ void k_particle_momentum_final(int d, const double* __restrict__ part
 // Per-particle constants from the diameter (held in rad on entry) and the
 // density ratio (held in buoy on entry): radius, mass (rho_p pi d^2/4 per unit
 // depth in 2D, rho_p pi d^3/6 in 3D, rho_f = 1), cross-section A_p = pi d^2/4
-// (section 2.2) and the buoyancy-reduced weight factor m (1 - rho_f/rho_p) of
-// Eq. (13).
+// (section 2.2), the buoyancy-reduced weight factor m (1 - rho_f/rho_p) of
+// Eq. (13), the linear-law wall damping and their FP32 copies; the particles are
+// numbered in user order.
 __global__ void k_particle_init(long long np, int d, double kn, double beta,
                                 double* __restrict__ rad, double* __restrict__ mass,
                                 double* __restrict__ Ap, double* __restrict__ buoy,
-                                double* __restrict__ gw, float* __restrict__ radf) {
+                                double* __restrict__ gw, float4* __restrict__ cf,
+                                unsigned* __restrict__ pid) {
   long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= np) return;
+  pid[p] = (unsigned)p;
   const double dia = rad[p], rr = buoy[p];
   const double pi = 3.14159265358979323846;
   const double m = d == 2 ? rr * pi * dia * dia / 4.0 : rr * pi * dia * dia * dia / 6.0;
+  const double a = pi * dia * dia / 4.0, b = m * (1.0 - 1.0 / rr);
   rad[p] = 0.5 * dia;
-  radf[p] = (float)(0.5 * dia);
   mass[p] = m;
-  Ap[p] = pi * dia * dia / 4.0;
-  buoy[p] = m * (1.0 - 1.0 / rr);
+  Ap[p] = a;
+  buoy[p] = b;
   gw[p] = 2.0 * beta * sqrt(m * kn);
+  cf[p] = make_float4((float)m, (float)a, (float)b, (float)(0.5 * dia));
 }
 
 unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -878,10 +1277,10 @@ cudaError_t launch_bin(const State& s, cudaStream_t st, int* nk) {
   if (e != cudaSuccess) return e;
   const double* X = P.X[s.cur];
   if (s.geo.d == 2)
-    k_bin_key<2><<<blocks_for(P.np, 256), 256, 0, st>>>(X, P.np, s.geo, P.bm, P.radf, P.key,
+    k_bin_key<2><<<blocks_for(P.np, 256), 256, 0, st>>>(X, P.np, s.geo, P.bm, P.cf[s.cur], P.key,
                                                         P.rank, P.bin_cnt, P.xr, P.cr);
   else
-    k_bin_key<3><<<blocks_for(P.np, 256), 256, 0, st>>>(X, P.np, s.geo, P.bm, P.radf, P.key,
+    k_bin_key<3><<<blocks_for(P.np, 256), 256, 0, st>>>(X, P.np, s.geo, P.bm, P.cf[s.cur], P.key,
                                                         P.rank, P.bin_cnt, P.xr, P.cr);
   const long long n = P.nbin + 1;
   k_scan_reduce<<<P.scan_blocks, SCAN_THREADS, 0, st>>>(P.bin_cnt, n, P.block_sums);
@@ -891,7 +1290,7 @@ cudaError_t launch_bin(const State& s, cudaStream_t st, int* nk) {
                                                        P.cr, P.perm, P.xs, P.cs);
   if (nk) *nk += 5;
   if (s.deterministic) {
-    // bins in particle-id order: every sum over a bin then runs in a fixed order
+    // bins in storage order: every sum over a bin then runs in a fixed order
     k_bin_sort<<<blocks_for(P.np, 256), 256, 0, st>>>(P.key, P.rank, P.bin_cnt, P.np, P.xr,
                                                       P.cr, P.perm, P.xs, P.cs);
     if (nk) *nk += 1;
@@ -911,18 +1310,30 @@ CoupleArgs couple_args(const State& s) {
   A.U = P.U[s.cur];
   A.Xn = P.X[1 - s.cur];
   A.Un = P.U[1 - s.cur];
-  A.rad = P.rad;
-  A.mass = P.mass;
-  A.Ap = P.Ap;
-  A.buoy = P.buoy;
-  A.gw = P.gw;
-  A.radf = P.radf;
+  const int c = s.cur, n = 1 - s.cur;
+  A.rad = P.rad[c];
+  A.mass = P.mass[c];
+  A.Ap = P.Ap[c];
+  A.buoy = P.buoy[c];
+  A.gw = P.gw[c];
+  A.cf = P.cf[c];
+  A.pid = P.pid[c];
+  A.radn = P.rad[n];
+  A.massn = P.mass[n];
+  A.Apn = P.Ap[n];
+  A.buoyn = P.buoy[n];
+  A.gwn = P.gw[n];
+  A.cfn = P.cf[n];
+  A.pidn = P.pid[n];
   A.xs = P.xs;
   A.cs = P.cs;
   // in-cell offsets are exact to 2^-24 and whole-cell differences exactly so
   A.xf_margin = 1e-5f;
   A.gout = P.g;
   A.Fcout = P.Fc;
+  A.rl = P.rl;
+  A.jl = P.jl;
+  A.Fs = P.Fs;
   A.perm = P.perm;
   A.start = P.bin_cnt;
   A.f = s.f[s.cur];
@@ -940,18 +1351,46 @@ cudaError_t couple_t(const State& s, cudaStream_t st, int* nk) {
   using T = typename St::T;
   using R = typename St::R;
   CoupleArgs A = couple_args(s);
-  const unsigned ntiles = (unsigned)(P.nbin / P.bm.tc);
-  k_moments<Q, St><<<ntiles, 256, 0, st>>>(s.geo, P.bm, P.bin_cnt, (const T*)s.f[s.cur],
-                                           (R*)s.mom);
-  k_couple<Q, W, St, FT><<<blocks_for(P.np, 256), 256, 0, st>>>(A);
-  if (nk) *nk += 2;
+  const long long ntiles = P.nbin / P.bm.tc;
+  constexpr int KT = MomentsShape<Q, St>::KT;
+  const unsigned pb = blocks_for(P.np, 256);
+  k_moments<Q, St><<<(unsigned)((ntiles + KT - 1) / KT), 256, 0, st>>>(
+      s.geo, P.bm, P.bin_cnt, (const T*)s.f[s.cur], (R*)s.mom);
+  int n = 1;
+  if (s.phy.substeps <= 1) {
+    if (s.phy.lagrange)
+      k_couple<Q, W, St, FT, true><<<pb, 256, 0, st>>>(A);
+    else
+      k_couple<Q, W, St, FT, false><<<pb, 256, 0, st>>>(A);
+    n += 1;
+  } else {
+    // DEM sub-cycling: interpolate once, S x (contacts, update), then spread
+    if (s.phy.lagrange)
+      k_sub_init<Q, 4, St, true><<<pb, 256, 0, st>>>(A);
+    else
+      k_sub_init<Q, W, St, false><<<pb, 256, 0, st>>>(A);
+    const double h = 1.0 / (double)s.phy.substeps;
+    for (int k = 0; k < s.phy.substeps; ++k) {
+      if (s.phy.hertz)
+        k_contacts<D, true, true><<<pb, 256, 0, st>>>(A);
+      else
+        k_contacts<D, true, false><<<pb, 256, 0, st>>>(A);
+      k_substep<D><<<pb, 256, 0, st>>>(A, h);
+    }
+    n += 1 + 2 * s.phy.substeps;
+    if (A.spread) {
+      k_sub_spread<Q, W, St, FT><<<pb, 256, 0, st>>>(A);
+      n += 1;
+    }
+  }
+  if (nk) *nk += n;
   if (s.deterministic) {
     const Geometry& g = s.geo;
     int bx = g.n[0] <= 32 ? 32 : (g.n[0] <= 64 ? 64 : 128);
     dim3 blk(bx, 256 / bx, 1);
     dim3 grd((g.n[0] + blk.x - 1) / blk.x, (g.n[1] + blk.y - 1) / blk.y, g.n[2]);
-    k_spread_gather<D, W, FT><<<grd, blk, 0, st>>>(g, P.bm, P.np, P.X[s.cur], P.Ap, P.g, P.perm,
-                                                   P.bin_cnt, (FT*)s.F);
+    k_spread_gather<D, W, FT><<<grd, blk, 0, st>>>(g, P.bm, P.np, P.X[s.cur], P.Ap[s.cur], P.g,
+                                                   P.perm, P.bin_cnt, (FT*)s.F);
     if (nk) *nk += 1;
   }
   return cudaGetLastError();
@@ -964,12 +1403,17 @@ cudaError_t couple_w(const State& s, cudaStream_t st, int* nk) {
 }  // namespace
 
 cudaError_t launch_contacts(const State& s, cudaStream_t st, int* nk) {
-  if (s.p.np == 0) return cudaSuccess;
+  // with DEM sub-cycling the contacts run inside the particle phase, per sub-step
+  if (s.p.np == 0 || s.phy.substeps > 1) return cudaSuccess;
   CoupleArgs A = couple_args(s);
-  if (s.geo.d == 2)
-    k_contacts<2><<<blocks_for(s.p.np, 256), 256, 0, st>>>(A);
-  else
-    k_contacts<3><<<blocks_for(s.p.np, 256), 256, 0, st>>>(A);
+  const unsigned pb = blocks_for(s.p.np, 256);
+  if (s.geo.d == 2) {
+    if (s.phy.hertz) k_contacts<2, false, true><<<pb, 256, 0, st>>>(A);
+    else k_contacts<2, false, false><<<pb, 256, 0, st>>>(A);
+  } else {
+    if (s.phy.hertz) k_contacts<3, false, true><<<pb, 256, 0, st>>>(A);
+    else k_contacts<3, false, false><<<pb, 256, 0, st>>>(A);
+  }
   if (nk) *nk += 1;
   return cudaGetLastError();
 }
@@ -999,14 +1443,16 @@ cudaError_t launch_couple(const State& s, cudaStream_t st, int* nk) {
 
 cudaError_t launch_particle_forces(const State& s, double* f_fpi, double* f_c, cudaStream_t st) {
   if (s.p.np == 0) return cudaSuccess;
-  k_forces<<<blocks_for(s.p.np, 256), 256, 0, st>>>(s.p.np, s.geo.d, s.p.Ap, s.p.g, s.p.Fc, f_fpi,
-                                                    f_c);
+  const Particles& P = s.p;
+  k_forces<<<blocks_for(P.np, 256), 256, 0, st>>>(P.np, s.geo.d, P.Ap[s.cur], P.g, P.Fc,
+                                                  P.pid[s.cur], f_fpi, f_c, s.err);
   return cudaGetLastError();
 }
 
 cudaError_t launch_interleave(const State& s, const double* soa, double* aos, cudaStream_t st) {
   if (s.p.np == 0) return cudaSuccess;
-  k_interleave<<<blocks_for(s.p.np, 256), 256, 0, st>>>(s.p.np, s.geo.d, soa, aos);
+  k_interleave<<<blocks_for(s.p.np, 256), 256, 0, st>>>(s.p.np, s.geo.d, soa, s.p.pid[s.cur],
+                                                        aos, s.err);
   return cudaGetLastError();
 }
 
@@ -1016,7 +1462,7 @@ cudaError_t launch_particle_momentum(const State& s, double* out_dev, cudaStream
   if (s.p.np == 0) {
     return cudaMemsetAsync(out_dev, 0, sizeof(double) * s.geo.d, st);
   }
-  k_particle_momentum<<<PRED_BLOCKS, PRED_THREADS, 0, st>>>(s.p.np, s.geo.d, s.p.mass,
+  k_particle_momentum<<<PRED_BLOCKS, PRED_THREADS, 0, st>>>(s.p.np, s.geo.d, s.p.mass[s.cur],
                                                             s.p.U[s.cur], partial);
   k_particle_momentum_final<<<1, 32, 0, st>>>(s.geo.d, partial, out_dev);
   return cudaGetLastError();
@@ -1024,9 +1470,10 @@ cudaError_t launch_particle_momentum(const State& s, double* out_dev, cudaStream
 
 cudaError_t launch_particle_init(const State& s, cudaStream_t st) {
   if (s.p.np == 0) return cudaSuccess;
-  k_particle_init<<<blocks_for(s.p.np, 256), 256, 0, st>>>(s.p.np, s.geo.d, s.phy.kn,
-                                                           s.phy.beta, s.p.rad, s.p.mass,
-                                                           s.p.Ap, s.p.buoy, s.p.gw, s.p.radf);
+  const Particles& P = s.p;
+  k_particle_init<<<blocks_for(P.np, 256), 256, 0, st>>>(P.np, s.geo.d, s.phy.kn, s.phy.beta,
+                                                         P.rad[0], P.mass[0], P.Ap[0], P.buoy[0],
+                                                         P.gw[0], P.cf[0], P.pid[0]);
   return cudaGetLastError();
 }
 

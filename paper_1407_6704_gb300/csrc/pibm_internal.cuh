@@ -206,6 +206,7 @@ enum : unsigned {
   ERR_PARTICLE_NONFINITE = 2u,
   ERR_ESCAPED = 4u,
   ERR_INDEX = 8u,  // an internal index check failed; the access was skipped
+  ERR_SKIN = 16u,  // a particle moved farther than the cell list allows within a step
 };
 
 // ---------------------------------------------------------------------------
@@ -222,9 +223,16 @@ struct Geometry {
 struct Physics {
   double tau, omega, cF;  // omega = 1/tau, cF = 1 - omega/2 (Guo prefactor)
   double gravity[3];
+  float gravityf[3];       // the same in FP32 (FP32-storage particle increments)
   double kn, beta;        // contact stiffness; damping ratio from restitution
-  int width;              // 2 or 4
+  int width;              // 2 or 4 (spreading, and interpolation unless lagrange)
   int implicit_drag;
+  int lagrange;           // 1: interpolate with the 4-point Lagrange polynomials (Eq. 5)
+  int hertz;              // 1: Hertz normal contact (Eq. 15)
+  double Epp, Epw;        // Hertz: effective modulus particle-particle, particle-wall
+  double hz_damp;         // Hertz: 2 sqrt(5/6) beta
+  int substeps;           // DEM sub-steps per fluid step (>= 1)
+  double skin;            // largest displacement within a sub-cycled step, (1 - d_max) / 2
 };
 
 // Tile of lattice cells handled by one CTA of the particle kernel.
@@ -243,27 +251,38 @@ struct BinMap {
   int tc;
 };
 
+// Particle state is stored in cell-sorted order: the coupling kernel writes the
+// state of step n + 1 (and each particle's constants and user id) at the particle's
+// slot in the cell list of step n, so the next step's sort is nearly the identity
+// and every per-particle access of binning, contacts and coupling is nearly
+// coalesced. Every array with two buffers is indexed by storage position; pid maps
+// a storage position to the user's particle index.
 struct Particles {
   long long np;
   double* X[2];   // [d][np] SoA, ping-pong
   double* U[2];
-  double* rad;    // radius
-  double* mass;   // rho_r * (pi d^2 / 4) in 2D, rho_r * (pi d^3 / 6) in 3D
-  double* Ap;     // cross-section pi d^2 / 4
-  double* buoy;   // mass * (1 - 1 / rho_r)
-  double* gw;     // wall damping coefficient 2 beta sqrt(mass kn)
-  float* radf;    // radius in FP32 (contact pre-filter)
-  float4* xr;     // [np] FP32 in-cell position and radius by particle id (binning)
-  int4* cr;       // [np] cell (x, y, z) and particle id, by particle id (binning)
+  double* rad[2];   // radius
+  double* mass[2];  // rho_r * (pi d^2 / 4) in 2D, rho_r * (pi d^3 / 6) in 3D
+  double* Ap[2];    // cross-section pi d^2 / 4
+  double* buoy[2];  // mass * (1 - 1 / rho_r)
+  double* gw[2];    // wall damping coefficient 2 beta sqrt(mass kn)
+  float4* cf[2];    // FP32 {mass, A_p, buoy, radius} (FP32 arithmetic, contact pre-filter)
+  unsigned* pid[2];  // user index of the particle at each storage position
+  float4* xr;     // [np] FP32 in-cell position and radius by storage position (binning)
+  int4* cr;       // [np] cell (x, y, z) and storage position (binning)
   float4* xs;     // [np] xr in sorted (slot) order
   int4* cs;       // [np] cr in sorted (slot) order
-  double* g;      // [d][np] force density of the last step (Eq. 7)
-  double* Fc;     // [d][np] contact force of the last step
+  double* g;      // [d][np] force density of the last step (Eq. 7), by slot of that step
+  double* Fc;     // [d][np] contact force of the last step, by slot of that step
+  // DEM sub-cycling scratch, by slot (allocated when substeps > 1)
+  double* rl;     // [np] interpolated rho_l of the step
+  double* jl;     // [d][np] interpolated j_l of the step
+  double* Fs;     // [d][np] contact force of the current sub-step
   // cell list (bins = lattice cells)
   unsigned* key;      // [np] bin of each particle
   unsigned* rank;     // [np] arrival rank inside the bin
   unsigned* bin_cnt;  // [nbin + 1] counts, then exclusive prefix (bin start)
-  unsigned* perm;     // [np] particle id by sorted slot
+  unsigned* perm;     // [np] storage position by sorted slot
   unsigned* block_sums;  // scan scratch
   BinMap bm;
   long long nbin;         // tiles * cells per tile (>= ncell)
@@ -307,9 +326,11 @@ cudaError_t launch_bin(const State& s, cudaStream_t st, int* nkernels);
 cudaError_t launch_contacts(const State& s, cudaStream_t st, int* nkernels);
 cudaError_t launch_couple(const State& s, cudaStream_t st, int* nkernels);
 cudaError_t launch_particle_forces(const State& s, double* f_fpi, double* f_c, cudaStream_t st);
+// X or U of the current state (SoA by storage position) into aos[user index][d].
 cudaError_t launch_interleave(const State& s, const double* soa, double* aos, cudaStream_t st);
-// Derive radius, mass, A_p and buoyancy factor; expects diameter in p.rad and
-// the density ratio in p.buoy on entry.
+// Derive radius, mass, A_p and buoyancy factor in buffer 0 and number the
+// particles in user order; expects the diameter in p.rad[0] and the density ratio
+// in p.buoy[0] on entry.
 cudaError_t launch_particle_init(const State& s, cudaStream_t st);
 
 // Reductions in a fixed order (deterministic). The reduction scratch s.red holds

@@ -42,7 +42,13 @@ class Pibm:
 
     def __init__(self, lattice, n, periodic, tau, gravity=None, delta_width=2, implicit=True,
                  precision="fp64", deterministic=False, kn=1e-2, restitution=0.9, x0=None,
-                 u0=None, diameter=None, density_ratio=None, f0=None, device=None, stream=None):
+                 u0=None, diameter=None, density_ratio=None, f0=None, device=None, stream=None,
+                 interp="delta", contact="linear", young=1.0, poisson=0.3, wall_young=None,
+                 wall_poisson=None, substeps=1):
+        """interp: "delta" (the spreading kernel) or "lagrange4" (Eq. 5);
+        contact: "linear" (kn) or "hertz" (Eq. 15 with young/poisson of the
+        particles and of the walls, default the particles'); both use the
+        restitution coefficient; substeps: DEM sub-steps per fluid step."""
         import torch
 
         self._torch = torch
@@ -70,7 +76,11 @@ class Pibm:
             _lib.PIBM_IMPLICIT if implicit else _lib.PIBM_EXPLICIT, _PRECISION[precision],
             int(bool(deterministic)), float(kn), float(restitution), np_,
             _dptr(self._x0), _dptr(self._u0), _dptr(self._dia), _dptr(self._rr),
-            _dptr(self._f0))
+            _dptr(self._f0),
+            {"delta": _lib.PIBM_INTERP_DELTA, "lagrange4": _lib.PIBM_INTERP_LAGRANGE4}[interp],
+            {"linear": _lib.PIBM_DEM_LINEAR, "hertz": _lib.PIBM_DEM_HERTZ}[contact],
+            float(young), float(poisson), float(wall_young or 0.0),
+            float(poisson if wall_poisson is None else wall_poisson), int(substeps))
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
             else torch.device(device)
         nbytes = ctypes.c_size_t()

@@ -172,7 +172,8 @@ def test_deterministic_mode_parity_and_bitwise_repeat():
 
 
 def test_fp32_path_against_fp64_oracle():
-    """Populations stored as f - w in FP32 with FP32 collision; particles FP64.
+    """Populations stored as f - w in FP32 with FP32 collision; particle state
+    and contacts FP64, the per-step particle increment in FP32.
     Each step rounds the stored deviation to 24 bits (relative 6e-8 of |f - w|),
     so after 100 steps the velocity field stays within 1e-4 (relative L2)."""
     c = make_case(q=9, n=(40, 34), periodic=(0, 0), tau=0.7, width=4, npart=100, seed=24,
