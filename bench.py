@@ -48,22 +48,23 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _src_hash():
+def _src_hash(source):
+    """Hash of the source file that defines a kernel (csrc/<source>)."""
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1407_6704_gb300", "csrc", "*"))):
-        with open(p, "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(ROOT, "paper_1407_6704_gb300", "csrc", source), "rb") as fh:
+        h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def _traffic(kernel, workload):
-    """DRAM bytes per launch from a committed ncu summary, only if the kernel
-    sources are unchanged since it was captured."""
+    """DRAM bytes per launch from a committed ncu summary, only if the source
+    file of the kernel is unchanged since it was captured."""
     try:
         with open(TRAFFIC_FILE) as fh:
             t = json.load(fh)
         ent = t.get(kernel)
-        if ent and ent.get("workload") == workload and ent.get("source_sha") == _src_hash():
+        if (ent and ent.get("workload") == workload
+                and ent.get("source_sha") == _src_hash(ent["source"])):
             return float(ent["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -131,8 +132,36 @@ def collide_bytes_per_cell(q, precision):
 
 
 def particle_bytes(d):
-    # read X, U, d_p and write X, U in FP64: (4 d + 1) * 8 bytes per particle
-    return (4 * d + 1) * 8
+    # per particle, FP64: read X, U, F_c and the constants m, A_p, m (1 - 1/rho_r);
+    # write X', U' and g: (6 d + 3) * 8 bytes
+    return (6 * d + 3) * 8
+
+
+def stencil_cell_bytes(q, d, precision):
+    # per lattice cell inside some particle's delta stencil: the Q populations the
+    # interpolation reads and the d force components the spreading writes
+    s = 8 if precision == "fp64" else 4
+    return q * s + d * s
+
+
+def stencil_cells(X, n, width):
+    """Number of distinct lattice cells covered by the particles' width-point
+    delta stencils (walls drop the outside nodes)."""
+    import numpy as np
+    n = np.asarray(n[:X.shape[1]])
+    first = np.floor(X - 0.5).astype(np.int64) - (1 if width == 4 else 0)
+    ids = None
+    for offs in np.ndindex(*([width] * X.shape[1])):
+        c = first + np.asarray(offs)
+        ok = np.all((c >= 0) & (c < n), axis=1)
+        flat = np.zeros(len(X), dtype=np.int64)
+        stride = 1
+        for k in range(X.shape[1]):
+            flat += c[:, k] * stride
+            stride *= int(n[k])
+        flat = flat[ok]
+        ids = flat if ids is None else np.concatenate([ids, flat])
+    return int(np.unique(ids).size)
 
 
 def collide_flops_per_cell_fp64(q):
@@ -158,6 +187,7 @@ def run_gpu(args, rank, world):
     # replicas: each rank sedimentes its own independent instance
     w.seed = w.seed + 1000 * rank
     X, dia, rr = workload_particles(w)
+    n_stencil = stencil_cells(X, w.n, w.delta_width)
     peak_gbs, peak_src = _peaks()
     props = torch.cuda.get_device_properties(local)
     dev_id = str(getattr(props, "uuid", local))
@@ -242,8 +272,10 @@ def run_gpu(args, rank, world):
     kern = {
         "collide_stream": dict(kernel="k_collide_stream", ms=ph["collide_stream"],
                                bytes=cells * algo_cell),
-        "couple": dict(kernel="k_couple", ms=ph["couple"],
-                       bytes=w.n_particles * particle_bytes(w.d)),
+        "couple": dict(kernel="k_moments + k_couple", ms=ph["couple"],
+                       bytes=w.n_particles * particle_bytes(w.d)
+                       + n_stencil * stencil_cell_bytes(w.q, w.d, prec),
+                       stencil_cells=n_stencil),
         "contacts": dict(kernel="k_contacts", ms=ph["contacts"], bytes=None),
         "bin": dict(kernel="k_bin_* + k_scan_*", ms=ph["bin"], bytes=None),
     }
