@@ -199,6 +199,28 @@ int pibm_kernels_per_step(pibm_t* h);
  * last). Synchronises the stream. Not part of the method; a timing aid. */
 int pibm_profile_steps(pibm_t* h, int64_t nsteps, double* phase_ms);
 
+/* Gradient of the mean settling velocity by the discrete adjoint of the
+ * coupled step (FP64). Runs nsteps steps of cfg from its initial state and
+ * returns in *loss the particles' mean velocity along the last axis after the
+ * last step, L = (1/N) sum_p U_p[d-1], and the exact derivatives of the computed
+ * L (the adjoint of every discrete operation of the step, Eqs. 2-13):
+ *   dtau: dL/dtau (one double; may be NULL),
+ *   drho: [n_particles] dL/d(density ratio of each particle) (may be NULL),
+ *   dx0:  [n_particles][d] dL/d(initial position) (may be NULL);
+ * all host pointers. The forward run is the library's deterministic step; the
+ * state is checkpointed every checkpoint_every steps and each stretch is
+ * replayed for the reverse sweep, which needs device memory for
+ * (ceil(nsteps / checkpoint_every) + checkpoint_every) copies of the workspace of
+ * pibm_workspace_bytes(cfg). The call allocates and frees that memory itself and
+ * returns when done, on `stream` (a cudaStream_t, NULL = legacy default).
+ * Supported: precision PIBM_FP64, PIBM_IMPLICIT, PIBM_INTERP_DELTA (width 2 or
+ * 4), PIBM_DEM_LINEAR, no sub-cycling, n_particles >= 1; else PIBM_ENOTSUP or
+ * PIBM_EINVAL. Contacts make L non-smooth where an overlap starts or ends; the
+ * result is the derivative of the branch the run took. Errors as pibm_create,
+ * PIBM_ENOMEM when the checkpoints do not fit, and the run's health status. */
+int pibm_settling_gradient(const pibm_config* cfg, int64_t nsteps, int64_t checkpoint_every,
+                           void* stream, double* loss, double* dtau, double* drho, double* dx0);
+
 /* Pick the block shape of the fused stream-collide kernel for this handle by
  * timing a fixed list of candidates on its stream (not part of the method; a
  * tuning aid). The timing runs leave the simulation state unchanged. block_xy

@@ -35,7 +35,8 @@ EXPORTS = ["pibm_workspace_bytes", "pibm_create", "pibm_step", "pibm_forces",
            "pibm_read_fields", "pibm_invariants", "pibm_status", "pibm_kernels_per_step",
            "pibm_destroy", "pibm_strerror", "pibm_profile_steps", "pibm_last_error",
            "pibm_fluid_sums_noalloc", "pibm_autotune", "pibm_ensemble_create",
-           "pibm_ensemble_step", "pibm_ensemble_status", "pibm_ensemble_destroy"]
+           "pibm_ensemble_step", "pibm_ensemble_status", "pibm_ensemble_destroy",
+           "pibm_settling_gradient"]
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -125,6 +126,8 @@ def load(path: str = LIB_PATH):
     L.pibm_ensemble_status.restype = ctypes.c_int
     L.pibm_ensemble_destroy.argtypes = [vp]
     L.pibm_ensemble_destroy.restype = None
+    L.pibm_settling_gradient.argtypes = [P, ctypes.c_int64, ctypes.c_int64, vp, _dp, _dp, _dp, _dp]
+    L.pibm_settling_gradient.restype = ctypes.c_int
     L.pibm_last_error.argtypes = []
     L.pibm_last_error.restype = ctypes.c_char_p
     _lib = L

@@ -35,7 +35,7 @@ constexpr size_t ALIGN = 256;
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-  size_t f, F, mom, red, err, out, X, U, rad, mass, Ap, buoy, gw, cf, pid, rl, jl, Fs, xr, cr, xs, cs, g, Fc, key, rank, perm, bin,
+  size_t f, F, mom, red, err, out, X, U, rad, mass, Ap, buoy, gw, cf, pid, rl, jl, Fs, ti, tw, xr, cr, xs, cs, g, Fc, key, rank, perm, bin,
       bsum;
   size_t total;
 };
@@ -161,6 +161,8 @@ Layout layout(const pibm_config* c) {
   L.rl = take(sub ? sizeof(double) * np : 0);
   L.jl = take(sub ? sizeof(double) * d * np : 0);
   L.Fs = take(sub ? sizeof(double) * d * np : 0);
+  L.ti = take(c->deterministic ? sizeof(int) * 12 * np : 0);
+  L.tw = take(c->deterministic ? sizeof(double) * 12 * np : 0);
   L.xr = take(sizeof(float4) * np);
   L.cr = take(sizeof(int4) * np);
   L.xs = take(sizeof(float4) * np);
@@ -268,6 +270,10 @@ struct DeviceGuard {
 };
 
 }  // namespace
+
+namespace pibm {
+HandleView handle_view(pibm_t* h) { return HandleView{&h->s, h->ws, h->ws_bytes, h->stream}; }
+}  // namespace pibm
 
 extern "C" {
 
@@ -416,6 +422,8 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
   P.rl = (double*)(base + L.rl);
   P.jl = (double*)(base + L.jl);
   P.Fs = (double*)(base + L.Fs);
+  P.ti = (int*)(base + L.ti);
+  P.tw = (double*)(base + L.tw);
   P.Fc = (double*)(base + L.Fc);
   P.key = (unsigned*)(base + L.key);
   P.rank = (unsigned*)(base + L.rank);

@@ -32,15 +32,6 @@ __device__ __forceinline__ int bin_coord(double X, int n) {
   return b < 0 ? 0 : (b >= n ? n - 1 : b);
 }
 
-template <int D>
-__device__ __forceinline__ unsigned bin_index(const BinMap& b, int x, int y, int z) {
-  using TD = TileDims<D>;
-  const int tx = x / TD::TX, ty = y / TD::TY, tz = z / TD::TZ;
-  const int lx = x - tx * TD::TX, ly = y - ty * TD::TY, lz = z - tz * TD::TZ;
-  return (unsigned)(tx + b.nt[0] * (ty + b.nt[1] * tz)) * (unsigned)TD::TC +
-         (unsigned)(lx + TD::TX * (ly + TD::TY * lz));
-}
-
 // Bins are lattice cells, numbered tile-major: the cells of one tile form a
 // contiguous bin range, so after sorting its particles form one contiguous range.
 template <int D>
@@ -325,16 +316,6 @@ __device__ __forceinline__ bool outside_bits(double v, double n) {
          (b < 0x8000000000000000ull && b > (unsigned long long)__double_as_longlong(n));
 }
 
-// Wrap a region coordinate onto the lattice: periodic axes wrap, wall axes
-// report cells outside [0, n).
-__device__ __forceinline__ bool lattice_coord(int& x, int n, int periodic) {
-  if (x >= 0 && x < n) return true;
-  if (!periodic) return false;
-  x %= n;
-  if (x < 0) x += n;
-  return true;
-}
-
 // The stored values that stream into lattice cell (x, y, z): f*(x - e_a, a), or
 // f*(x, opp a) (halfway bounce-back) where x - e_a lies beyond a wall.
 template <int Q, class St>
@@ -385,15 +366,6 @@ __device__ __forceinline__ void sum_moments(const typename St::T (&v)[Q], typena
   j[2] = m2;
 }
 
-__device__ __forceinline__ double min_image(double s, int n, int periodic) {
-  if (periodic) {
-    double N = (double)n;
-    if (s > 0.5 * N) s -= N;
-    if (s < -0.5 * N) s += N;
-  }
-  return s;
-}
-
 struct CoupleArgs {
   Geometry g;
   Physics ph;
@@ -427,6 +399,8 @@ struct CoupleArgs {
   double* rl;        // sub-cycling: [np] rho_l by slot
   double* jl;        // sub-cycling: [d][np] j_l by slot
   double* Fs;        // sub-cycling: [d][np] contact force of the sub-step by slot
+  int* ti;           // ordered spreading: [np][3][4] spreading tap cells by slot
+  double* tw;        // ordered spreading: [np][3][4] spreading tap weights by slot
   const unsigned* perm;
   const unsigned* start;
   const void* f;     // stored populations f*
@@ -864,6 +838,22 @@ __device__ __forceinline__ double advance_axis(double x, int n, int periodic, bo
   return x;
 }
 
+// Ordered spreading: keep the particle's spreading taps at its slot for the
+// gather kernel, which then applies exactly the weights the atomic path would.
+template <int D, int W, typename TW>
+__device__ __forceinline__ void keep_taps(const CoupleArgs& A, long long sl, const Taps<W, TW>& tx,
+                                          const Taps<W, TW>& ty, const Taps<W, TW>& tz) {
+  const Taps<W, TW>* t[3] = {&tx, &ty, &tz};
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const bool on = k < D && i < W;
+      A.ti[(sl * 3 + k) * 4 + i] = on ? t[k]->idx[i] : -1;
+      A.tw[(sl * 3 + k) * 4 + i] = on ? (double)t[k]->w[i] : 0.0;
+    }
+}
+
 // The particle's constants move with it to its slot.
 __device__ __forceinline__ void move_constants(const CoupleArgs& A, unsigned p, long long sl) {
   A.radn[sl] = A.rad[p];
@@ -994,13 +984,15 @@ __global__ void __launch_bounds__(256, (Lattice<Q>::D == 2 && sizeof(typename St
   }
 
   // --- spreading (Eq. 9) with the delta kernel ---
-  if (!A.spread || !act) return;
+  if (!act) return;
   if constexpr (LAG) {
     Taps<W, R> sx, sy, sz;
     particle_taps<D, W, false, R>(g, mc, mf, X, sx, sy, sz);
-    spread_amp<D, W, R, FT>(A, sx, sy, sz, amp);
+    if (A.spread) spread_amp<D, W, R, FT>(A, sx, sy, sz, amp);
+    else keep_taps<D, W, R>(A, sl, sx, sy, sz);
   } else {
-    spread_amp<D, W, R, FT>(A, tx, ty, tz, amp);
+    if (A.spread) spread_amp<D, W, R, FT>(A, tx, ty, tz, amp);
+    else keep_taps<D, W, R>(A, sl, tx, ty, tz);
   }
 }
 
@@ -1036,6 +1028,15 @@ __global__ void __launch_bounds__(256) k_sub_init(CoupleArgs A) {
   particle_taps<D, WI, LAG, R>(A.g, mc, mf, X, tx, ty, tz);
   R rs, js[3];
   gather_moments<D, WI, R>(A, tx, ty, tz, rs, js);
+  if (!A.spread) {  // ordered spreading at the end of the step: keep the taps
+    if constexpr (LAG) {
+      Taps<W, R> sx, sy, sz;
+      particle_taps<D, W, false, R>(A.g, mc, mf, X, sx, sy, sz);
+      keep_taps<D, W, R>(A, sl, sx, sy, sz);
+    } else {
+      keep_taps<D, W, R>(A, sl, tx, ty, tz);
+    }
+  }
   A.rl[sl] = (double)St::S + (double)rs;
 #pragma unroll
   for (int k = 0; k < D; ++k) A.jl[k * np + sl] = (double)js[k];
@@ -1118,11 +1119,13 @@ __global__ void __launch_bounds__(256) k_sub_spread(CoupleArgs A) {
 
 // Deterministic spreading: every cell gathers, in a fixed order (neighbour cells
 // by ascending z, y, x offset; particles by storage position inside a cell), the
-// A_p g w of every particle whose stencil covers it (X and A_p by storage
-// position, g by slot). Writes every cell of F.
+// A_p g w of every particle whose stencil covers it, with the taps the coupling
+// kernel kept at each slot (A_p by storage position, g and taps by slot).
+// Writes every cell of F.
 template <int D, int W, typename FT>
 __global__ void __launch_bounds__(256) k_spread_gather(Geometry g, BinMap bm, long long np,
-                                                       const double* __restrict__ X,
+                                                       const int* __restrict__ ti,
+                                                       const double* __restrict__ tw,
                                                        const double* __restrict__ Ap,
                                                        const double* __restrict__ gin,
                                                        const unsigned* __restrict__ perm,
@@ -1143,23 +1146,34 @@ __global__ void __launch_bounds__(256) k_spread_gather(Geometry g, BinMap bm, lo
     for (int oy = -R; oy <= R; ++oy) {
       int cy = y + oy;
       if (!lattice_coord(cy, g.n[1], g.periodic[1])) continue;
-#pragma unroll 1
-      for (int ox = -R; ox <= R; ++ox) {
-        int cx = x + ox;
-        if (!lattice_coord(cx, g.n[0], g.periodic[0])) continue;
-        const unsigned b = bin_index<D>(bm, cx, cy, cz);
-        const unsigned lo = start[b], hi = start[b + 1];
+      // the 2R + 1 cells of this row in ascending x: one run of consecutive bins
+      // when they are (the common case), else cell by cell; either way the
+      // particles are visited in the same order
+      constexpr int NX = 2 * R + 1;
+      unsigned b[NX];
+      bool ok[NX];
+      bool one = true;
+#pragma unroll
+      for (int i = 0; i < NX; ++i) {
+        int cx = x + i - R;
+        ok[i] = lattice_coord(cx, g.n[0], g.periodic[0]);
+        b[i] = ok[i] ? bin_index<D>(bm, cx, cy, cz) : 0u;
+        one = one && ok[i] && (i == 0 || b[i] == b[i - 1] + 1);
+      }
+#pragma unroll
+      for (int i = 0; i < NX; ++i) {
+        if (one ? i > 0 : !ok[i]) continue;
+        const unsigned lo = start[b[i]], hi = start[one ? b[NX - 1] + 1 : b[i] + 1];
         for (unsigned sl = lo; sl < hi; ++sl) {
           const unsigned p = perm[sl];
           FT wt = FT(1);
 #pragma unroll
           for (int k = 0; k < D; ++k) {
-            Taps<W, FT> t;
-            axis_taps<W, FT>(X[k * np + p], g.n[k], g.periodic[k], t);
             FT wk = FT(0);
 #pragma unroll
-            for (int i = 0; i < W; ++i)
-              if (t.idx[i] == cell[k]) wk += t.w[i];
+            for (int j = 0; j < W; ++j)
+              if (ti[((long long)sl * 3 + k) * 4 + j] == cell[k])
+                wk += (FT)tw[((long long)sl * 3 + k) * 4 + j];
             wt *= wk;
           }
           if (wt == FT(0)) continue;
@@ -1334,6 +1348,8 @@ CoupleArgs couple_args(const State& s) {
   A.rl = P.rl;
   A.jl = P.jl;
   A.Fs = P.Fs;
+  A.ti = P.ti;
+  A.tw = P.tw;
   A.perm = P.perm;
   A.start = P.bin_cnt;
   A.f = s.f[s.cur];
@@ -1389,7 +1405,7 @@ cudaError_t couple_t(const State& s, cudaStream_t st, int* nk) {
     int bx = g.n[0] <= 32 ? 32 : (g.n[0] <= 64 ? 64 : 128);
     dim3 blk(bx, 256 / bx, 1);
     dim3 grd((g.n[0] + blk.x - 1) / blk.x, (g.n[1] + blk.y - 1) / blk.y, g.n[2]);
-    k_spread_gather<D, W, FT><<<grd, blk, 0, st>>>(g, P.bm, P.np, P.X[s.cur], P.Ap[s.cur], P.g,
+    k_spread_gather<D, W, FT><<<grd, blk, 0, st>>>(g, P.bm, P.np, P.ti, P.tw, P.Ap[s.cur], P.g,
                                                    P.perm, P.bin_cnt, (FT*)s.F);
     if (nk) *nk += 1;
   }

@@ -278,6 +278,9 @@ struct Particles {
   double* rl;     // [np] interpolated rho_l of the step
   double* jl;     // [d][np] interpolated j_l of the step
   double* Fs;     // [d][np] contact force of the current sub-step
+  // ordered spreading (deterministic mode): each particle's spreading taps, by slot
+  int* ti;        // [np][3][4] cell index per axis and node
+  double* tw;     // [np][3][4] weight per axis and node
   // cell list (bins = lattice cells)
   unsigned* key;      // [np] bin of each particle
   unsigned* rank;     // [np] arrival rank inside the bin
@@ -303,6 +306,39 @@ struct State {
   int cur;        // index of the buffer holding the current f* / X / U
   int cblk[2];    // collide-stream block shape (x, y); 0 = built-in choice
 };
+
+// ---------------------------------------------------------------------------
+// Cell-list and geometry helpers shared by the particle kernels and the adjoint
+// ---------------------------------------------------------------------------
+// Bin of lattice cell (x, y, z): cells numbered tile-major (TileDims).
+template <int D>
+__device__ __forceinline__ unsigned bin_index(const BinMap& b, int x, int y, int z) {
+  using TD = TileDims<D>;
+  const int tx = x / TD::TX, ty = y / TD::TY, tz = z / TD::TZ;
+  const int lx = x - tx * TD::TX, ly = y - ty * TD::TY, lz = z - tz * TD::TZ;
+  return (unsigned)(tx + b.nt[0] * (ty + b.nt[1] * tz)) * (unsigned)TD::TC +
+         (unsigned)(lx + TD::TX * (ly + TD::TY * lz));
+}
+
+// Wrap a region coordinate onto the lattice: periodic axes wrap, wall axes
+// report cells outside [0, n).
+__device__ __forceinline__ bool lattice_coord(int& x, int n, int periodic) {
+  if (x >= 0 && x < n) return true;
+  if (!periodic) return false;
+  x %= n;
+  if (x < 0) x += n;
+  return true;
+}
+
+// Minimum-image separation along one axis (periodic axes).
+__device__ __forceinline__ double min_image(double s, int n, int periodic) {
+  if (periodic) {
+    double N = (double)n;
+    if (s > 0.5 * N) s -= N;
+    if (s < -0.5 * N) s += N;
+  }
+  return s;
+}
 
 // ---------------------------------------------------------------------------
 // Launchers (defined in lbm.cu, particles.cu, reduce.cu)
@@ -332,6 +368,19 @@ cudaError_t launch_interleave(const State& s, const double* soa, double* aos, cu
 // particles in user order; expects the diameter in p.rad[0] and the density ratio
 // in p.buoy[0] on entry.
 cudaError_t launch_particle_init(const State& s, cudaStream_t st);
+
+// Internal view of a handle (api.cu): its state, workspace and stream.
+struct HandleView {
+  State* s;
+  void* ws;
+  size_t ws_bytes;
+  cudaStream_t stream;
+};
+HandleView handle_view(pibm_t* h);
+
+// Gradient of the mean settling velocity by the discrete adjoint (adjoint.cu).
+int settling_gradient(const pibm_config* cfg, int64_t nsteps, int64_t K, void* stream,
+                      double* loss, double* dtau, double* drho, double* dx0);
 
 // Reductions in a fixed order (deterministic). The reduction scratch s.red holds
 // RED_SCRATCH doubles: fluid partials first, particle partials after them.

@@ -234,3 +234,74 @@ class Ensemble:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def settling_gradient(lattice, n, periodic, tau, nsteps, checkpoint_every=50, gravity=None,
+                      delta_width=2, kn=1e-2, restitution=0.9, x0=None, u0=None, diameter=None,
+                      density_ratio=None, f0=None, stream=None, grads=True):
+    """Mean settling velocity L = mean over particles of U[d-1] after nsteps FP64
+    steps, and its gradients by the discrete adjoint (``pibm_settling_gradient``):
+    {"loss", "dtau", "drho" (n_particles,), "dx0" (n_particles, d)}; with
+    grads=False only the forward run (the gradients come back as None)."""
+    import torch
+
+    q = _LATTICES[lattice]
+    d = 2 if q == 9 else 3
+    n = list(n) + [1] * (3 - len(n))
+    per = list(periodic) + [1] * (3 - len(periodic))
+    X = _f64(x0, (-1, d))
+    npart = X.shape[0]
+    U = _f64(u0, (npart, d)) if u0 is not None else None
+    dia = _f64(diameter, (npart,))
+    rr = _f64(density_ratio, (npart,))
+    F0 = _f64(f0, (q, -1)) if f0 is not None else None
+    grav = ((list(gravity) if gravity is not None else [0.0] * d) + [0.0, 0.0, 0.0])[:3]
+    cfg = PibmConfig(q, (ctypes.c_int64 * 3)(*n),
+                     (ctypes.c_int * 3)(*[_lib.PIBM_PERIODIC if p else _lib.PIBM_WALL for p in per]),
+                     float(tau), (ctypes.c_double * 3)(*grav), int(delta_width), _lib.PIBM_IMPLICIT,
+                     _lib.PIBM_FP64, 1, float(kn), float(restitution), npart, _dptr(X), _dptr(U),
+                     _dptr(dia), _dptr(rr), _dptr(F0))
+    st = stream if stream is not None else torch.cuda.current_stream()
+    loss = np.zeros(1)
+    dtau = np.zeros(1)
+    drho = np.zeros(npart)
+    dx0 = np.zeros((npart, d))
+    g = (lambda a: _dptr(a)) if grads else (lambda a: None)
+    check(_lib.load().pibm_settling_gradient(ctypes.byref(cfg), int(nsteps), int(checkpoint_every),
+                                             ctypes.c_void_p(st.cuda_stream), _dptr(loss),
+                                             g(dtau), g(drho), g(dx0)),
+          "pibm_settling_gradient")
+    if not grads:
+        return {"loss": float(loss[0]), "dtau": None, "drho": None, "dx0": None}
+    return {"loss": float(loss[0]), "dtau": float(dtau[0]), "drho": drho, "dx0": dx0}
+
+
+def _settling_function():
+    import torch
+
+    class SettlingVelocity(torch.autograd.Function):
+        """torch.autograd view of ``settling_gradient``: forward(tau, density_ratio,
+        x0, spec) returns the mean settling velocity as a 0-d FP64 tensor; backward
+        returns the adjoint gradients for tau, density_ratio and x0. ``spec`` holds
+        the remaining keyword arguments of ``settling_gradient``."""
+
+        @staticmethod
+        def forward(ctx, tau, density_ratio, x0, spec):
+            r = settling_gradient(tau=float(tau), density_ratio=density_ratio.detach().cpu().numpy(),
+                                  x0=x0.detach().cpu().numpy(), **spec)
+            ctx.grads = (torch.tensor(r["dtau"], dtype=torch.float64),
+                         torch.from_numpy(r["drho"]), torch.from_numpy(r["dx0"]))
+            return torch.tensor(r["loss"], dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, grad):
+            gt, gr, gx = ctx.grads
+            return grad * gt, grad * gr, grad * gx, None
+
+    return SettlingVelocity
+
+
+def settling_velocity(tau, density_ratio, x0, **spec):
+    """Differentiable mean settling velocity (see ``settling_gradient``) of CPU
+    FP64 tensors tau (0-d), density_ratio (n,), x0 (n, d)."""
+    return _settling_function().apply(tau, density_ratio, x0, spec)
