@@ -350,6 +350,8 @@ def run_gpu(args, rank, world):
                                            "frac": a / FP64_PEAK_TFLOPS}
     if args.ensemble:
         line["ensemble"] = ensemble_bench(args)
+    if args.adjoint:
+        line["adjoint"] = adjoint_bench()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, w)
     if dist is not None:
@@ -401,6 +403,33 @@ def ensemble_bench(args, k=None):
             "ms_per_step": ms_ens, "value": cells / (ms_ens * 1e-3) / 1e6, "unit": "MLUPS",
             "members_one_by_one_ms_per_step": ms_seq,
             "members_one_by_one_value": cells / (ms_seq * 1e-3) / 1e6, "status": status}
+
+
+def adjoint_bench(steps=500, K=50):
+    """The differentiable configuration: D3Q19 96^3, 20k particles, FP64, the
+    gradient of the mean settling velocity after 500 steps with respect to tau,
+    the density ratios and the initial positions (checkpoints every 50 steps),
+    timed against the forward run alone (wall clock around each call)."""
+    import torch
+    from paper_1407_6704_gb300.inputs import preset, workload_particles
+    from paper_1407_6704_gb300.pibm import settling_gradient
+
+    w = preset("c5")
+    X, dia, rr = workload_particles(w)
+    kw = dict(gravity=w.gravity, delta_width=w.delta_width, kn=w.kn, restitution=w.restitution,
+              x0=X, diameter=dia, density_ratio=rr)
+    settling_gradient("d3q19", w.n, w.periodic, w.tau, 20, checkpoint_every=10, **kw)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = settling_gradient("d3q19", w.n, w.periodic, w.tau, steps, checkpoint_every=K, **kw)
+    t1 = time.perf_counter()
+    f = settling_gradient("d3q19", w.n, w.periodic, w.tau, steps, grads=False, **kw)
+    t2 = time.perf_counter()
+    return {"workload": "D3Q19 96^3 walls, tau 0.7, 20k particles d 0.5 ratio 2, FP64, 500 steps",
+            "checkpoint_every": K, "loss": g["loss"], "dloss_dtau": g["dtau"],
+            "gradient_s": t1 - t0, "forward_s": t2 - t1,
+            "gradient_over_forward": (t1 - t0) / (t2 - t1),
+            "loss_matches_forward": g["loss"] == f["loss"]}
 
 
 def cpu_sample(w, side=256):
@@ -495,6 +524,8 @@ def main():
     ap.add_argument("--both", type=int, default=1, help="also time the other precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ensemble", type=int, default=1, help="also time the 64-member ensemble")
+    ap.add_argument("--adjoint", type=int, default=1,
+                    help="also time the 500-step gradient of the 96^3 FP64 configuration")
     ap.add_argument("--profile-only", action="store_true",
                     help="only run --steps phase-by-phase steps (ncu driver); prints phase times")
     args = ap.parse_args()
