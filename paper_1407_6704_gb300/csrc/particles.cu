@@ -865,15 +865,95 @@ __device__ __forceinline__ void move_constants(const CoupleArgs& A, unsigned p, 
   A.pidn[sl] = A.pid[p];
 }
 
+// Particle update (Eq. 13) and force density (Eqs. 6-7) of the particle at slot
+// sl (storage position p), from the interpolated rs = sum w (rho - S) and js and
+// the contact force: writes X', U', g and the particle's constants at the slot
+// and returns A_p g in amp. FP64 mode solves the update in FP64. The
+// FP32-storage modes (whose rho_l, j_l come from FP32 moments) form the velocity
+// increment U' - U and g in FP32 and add the increment to the FP64 state.
+template <int D, class St, typename FT>
+__device__ __forceinline__ void advance_particle(const CoupleArgs& A, long long sl, unsigned p,
+                                                 const double (&X)[3], const double (&U)[3],
+                                                 const double (&Fc)[3], typename St::R rs,
+                                                 const typename St::R (&js)[3], FT (&amp)[3]) {
+  using R = typename St::R;
+  const Geometry& g = A.g;
+  const long long np = A.np;
+  double Un[3];
+  bool bad = false, esc = false;
+  if constexpr (sizeof(R) == 8) {
+    const double mi = A.mass[p], Ap = A.Ap[p], bu = A.buoy[p];
+    const double rho_l = (double)St::S + rs;
+    double Ub[3];
+    if (A.ph.implicit_drag) {
+      const double inv = rcp_newton<2>(mi + 2.0 * Ap * rho_l);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        Un[k] = (mi * U[k] + 2.0 * Ap * js[k] + bu * A.ph.gravity[k] + Fc[k]) * inv;
+        Ub[k] = Un[k];
+      }
+    } else {
+      const double invm = 1.0 / mi;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        Un[k] = U[k] + (bu * A.ph.gravity[k] + Fc[k] - Ap * 2.0 * (rho_l * U[k] - js[k])) * invm;
+        Ub[k] = U[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const double gg = 2.0 * (rho_l * Ub[k] - js[k]);
+      amp[k] = (FT)(Ap * gg);
+      A.gout[k * np + sl] = gg;
+    }
+  } else {
+    const float4 cc = A.cf[p];  // mass, A_p, buoy, radius
+    const float rho = (float)St::S + rs;
+    float Uf[3], dU[3], Ub[3];
+#pragma unroll
+    for (int k = 0; k < D; ++k) Uf[k] = (float)U[k];
+    if (A.ph.implicit_drag) {
+      // U' - U = (2 A_p (j_l - rho_l U) + buoy g + F_c) / (m + 2 A_p rho_l)
+      const float inv = 1.f / (cc.x + 2.f * cc.y * rho);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        dU[k] = (2.f * cc.y * (js[k] - rho * Uf[k]) + cc.z * A.ph.gravityf[k] + (float)Fc[k]) * inv;
+        Ub[k] = Uf[k] + dU[k];
+      }
+    } else {
+      const float invm = 1.f / cc.x;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        dU[k] = (cc.z * A.ph.gravityf[k] + (float)Fc[k] - 2.f * cc.y * (rho * Uf[k] - js[k])) * invm;
+        Ub[k] = Uf[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      Un[k] = U[k] + (double)dU[k];
+      const float gg = 2.f * (rho * Ub[k] - js[k]);
+      amp[k] = (FT)(gg * cc.y);
+      A.gout[k * np + sl] = (double)gg;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const double xn = advance_axis(X[k] + Un[k], g.n[k], g.periodic[k], esc);
+    bad |= not_finite_bits(xn) || not_finite_bits(Un[k]);
+    A.Xn[k * np + sl] = xn;
+    A.Un[k * np + sl] = Un[k];
+  }
+  if (bad) atomicOr(A.err, ERR_PARTICLE_NONFINITE);
+  if (esc) atomicOr(A.err, ERR_ESCAPED);
+  move_constants(A, p, sl);
+}
+
 // Particle coupling, one thread per particle in cell-sorted order: interpolate
 // rho, j from the moment field (Eq. 4; the delta kernel, or Eq. 5 when LAG),
 // take the contact force (k_contacts), advance U and X (Eq. 13), form
 // g = 2 (rho_l U_b - j_l) (Eqs. 6-7) and spread A_p g w into F (Eq. 9) with the
 // delta kernel of width W. The new state, g and the particle's constants are
 // written at its slot, which becomes its storage position for the next step.
-// FP64 mode solves the update in FP64. The FP32-storage modes (whose rho_l, j_l
-// come from FP32 moments) form the velocity increment U' - U and g in FP32 and
-// add the increment to the FP64 state: positions and velocities stay FP64.
 template <int Q, int W, class St, typename FT, bool LAG>
 __global__ void __launch_bounds__(256, (Lattice<Q>::D == 2 && sizeof(typename St::R) == 4) ? 5 : 1)
     k_couple(CoupleArgs A) {
@@ -914,73 +994,7 @@ __global__ void __launch_bounds__(256, (Lattice<Q>::D == 2 && sizeof(typename St
     gather_moments<D, WI, R>(A, tx, ty, tz, rs, js);
 
     // --- particle update (Eq. 13) and force density (Eqs. 6-7) ---
-    double Un[3];
-    bool bad = false, esc = false;
-    if constexpr (sizeof(R) == 8) {
-      const double mi = A.mass[p], Ap = A.Ap[p], bu = A.buoy[p];
-      const double rho_l = (double)St::S + rs;
-      double Ub[3];
-      if (A.ph.implicit_drag) {
-        const double inv = rcp_newton<2>(mi + 2.0 * Ap * rho_l);
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          Un[k] = (mi * U[k] + 2.0 * Ap * js[k] + bu * A.ph.gravity[k] + Fc[k]) * inv;
-          Ub[k] = Un[k];
-        }
-      } else {
-        const double invm = 1.0 / mi;
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          Un[k] = U[k] + (bu * A.ph.gravity[k] + Fc[k] - Ap * 2.0 * (rho_l * U[k] - js[k])) * invm;
-          Ub[k] = U[k];
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        const double gg = 2.0 * (rho_l * Ub[k] - js[k]);
-        amp[k] = (FT)(Ap * gg);
-        A.gout[k * np + sl] = gg;
-      }
-    } else {
-      const float4 cc = A.cf[p];  // mass, A_p, buoy, radius
-      const float rho = (float)St::S + rs;
-      float Uf[3], dU[3], Ub[3];
-#pragma unroll
-      for (int k = 0; k < D; ++k) Uf[k] = (float)U[k];
-      if (A.ph.implicit_drag) {
-        // U' - U = (2 A_p (j_l - rho_l U) + buoy g + F_c) / (m + 2 A_p rho_l)
-        const float inv = 1.f / (cc.x + 2.f * cc.y * rho);
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          dU[k] = (2.f * cc.y * (js[k] - rho * Uf[k]) + cc.z * A.ph.gravityf[k] + (float)Fc[k]) * inv;
-          Ub[k] = Uf[k] + dU[k];
-        }
-      } else {
-        const float invm = 1.f / cc.x;
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          dU[k] = (cc.z * A.ph.gravityf[k] + (float)Fc[k] - 2.f * cc.y * (rho * Uf[k] - js[k])) * invm;
-          Ub[k] = Uf[k];
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        Un[k] = U[k] + (double)dU[k];
-        const float gg = 2.f * (rho * Ub[k] - js[k]);
-        amp[k] = (FT)(gg * cc.y);
-        A.gout[k * np + sl] = (double)gg;
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      const double xn = advance_axis(X[k] + Un[k], g.n[k], g.periodic[k], esc);
-      bad |= not_finite_bits(xn) || not_finite_bits(Un[k]);
-      A.Xn[k * np + sl] = xn;
-      A.Un[k * np + sl] = Un[k];
-    }
-    if (bad) atomicOr(A.err, ERR_PARTICLE_NONFINITE);
-    if (esc) atomicOr(A.err, ERR_ESCAPED);
-    move_constants(A, p, sl);
+    advance_particle<D, St, FT>(A, sl, p, X, U, Fc, rs, js, amp);
   }
 
   // --- spreading (Eq. 9) with the delta kernel ---
@@ -1374,10 +1388,11 @@ cudaError_t couple_t(const State& s, cudaStream_t st, int* nk) {
       s.geo, P.bm, P.bin_cnt, (const T*)s.f[s.cur], (R*)s.mom);
   int n = 1;
   if (s.phy.substeps <= 1) {
-    if (s.phy.lagrange)
+    if (s.phy.lagrange) {
       k_couple<Q, W, St, FT, true><<<pb, 256, 0, st>>>(A);
-    else
+    } else {
       k_couple<Q, W, St, FT, false><<<pb, 256, 0, st>>>(A);
+    }
     n += 1;
   } else {
     // DEM sub-cycling: interpolate once, S x (contacts, update), then spread
