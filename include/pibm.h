@@ -54,7 +54,8 @@ extern "C" {
 #define PIBM_ENOMEM (-2)    /* workspace too small or allocation failed */
 #define PIBM_ECUDA (-3)     /* a CUDA call failed */
 #define PIBM_EUNSTABLE (-4) /* non-finite fluid or particle state detected, or a particle
-                               moved too far within one sub-cycled step */
+                               moved farther than the cell list allows (sub-cycling,
+                               rebin_every > 1) */
 #define PIBM_EESCAPED (-5)  /* a particle crossed a wall */
 #define PIBM_ENOTSUP (-6)   /* combination not built into this library */
 #define PIBM_EINTERNAL (-7) /* a device-side index check failed; the access was skipped */
@@ -144,6 +145,13 @@ typedef struct pibm_config {
                           (1 - largest diameter) / 2 so that the cell list of the step
                           start still holds every pair that can touch; a larger one
                           raises PIBM_EUNSTABLE. */
+  int rebin_every;     /* rebuild the cell list every R steps (0 or 1: every step). In
+                          between, the contact search and the ordered spreading use the
+                          bins of the last rebuild; this finds every touching pair as long
+                          as each particle stays within (1 - largest diameter) / 2 of the
+                          cell it had at the last rebuild, which is checked on the device
+                          every step (PIBM_EUNSTABLE when violated). Results equal those of
+                          R = 1 up to the summation order. Needs dem_substeps <= 1. */
 } pibm_config;
 
 typedef struct pibm_t pibm_t; /* opaque handle owning the device state */
@@ -188,8 +196,13 @@ int pibm_invariants(pibm_t* h, double* out);
 /* Synchronise the stream and return the device health status. */
 int pibm_status(pibm_t* h);
 
-/* Number of kernels one pibm_step(h, 1) launches (for launch accounting). */
+/* Number of kernels one pibm_step(h, 1) launches (for launch accounting); with
+ * rebin_every > 1, the count of a step that rebuilds the cell list. */
 int pibm_kernels_per_step(pibm_t* h);
+
+/* Total number of kernels pibm_step has launched on this handle since it was
+ * created (graph replays included), into *count. */
+int pibm_launch_count(pibm_t* h, int64_t* count);
 
 /* Advance nsteps steps like pibm_step, launched one phase at a time with CUDA
  * events between the phases, and return the summed device time of each phase
@@ -214,7 +227,7 @@ int pibm_profile_steps(pibm_t* h, int64_t nsteps, double* phase_ms);
  * pibm_workspace_bytes(cfg). The call allocates and frees that memory itself and
  * returns when done, on `stream` (a cudaStream_t, NULL = legacy default).
  * Supported: precision PIBM_FP64, PIBM_IMPLICIT, PIBM_INTERP_DELTA (width 2 or
- * 4), PIBM_DEM_LINEAR, no sub-cycling, n_particles >= 1; else PIBM_ENOTSUP or
+ * 4), PIBM_DEM_LINEAR, no sub-cycling, rebin_every <= 1, n_particles >= 1; else PIBM_ENOTSUP or
  * PIBM_EINVAL. Contacts make L non-smooth where an overlap starts or ends; the
  * result is the derivative of the branch the run took. Errors as pibm_create,
  * PIBM_ENOMEM when the checkpoints do not fit, and the run's health status. */

@@ -36,7 +36,7 @@ EXPORTS = ["pibm_workspace_bytes", "pibm_create", "pibm_step", "pibm_forces",
            "pibm_destroy", "pibm_strerror", "pibm_profile_steps", "pibm_last_error",
            "pibm_fluid_sums_noalloc", "pibm_autotune", "pibm_ensemble_create",
            "pibm_ensemble_step", "pibm_ensemble_status", "pibm_ensemble_destroy",
-           "pibm_settling_gradient"]
+           "pibm_settling_gradient", "pibm_launch_count"]
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -67,6 +67,7 @@ class PibmConfig(ctypes.Structure):
         ("wall_young", ctypes.c_double),
         ("wall_poisson", ctypes.c_double),
         ("dem_substeps", ctypes.c_int),
+        ("rebin_every", ctypes.c_int),
     ]
 
 
@@ -108,6 +109,8 @@ def load(path: str = LIB_PATH):
     L.pibm_status.restype = ctypes.c_int
     L.pibm_kernels_per_step.argtypes = [vp]
     L.pibm_kernels_per_step.restype = ctypes.c_int
+    L.pibm_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    L.pibm_launch_count.restype = ctypes.c_int
     L.pibm_profile_steps.argtypes = [vp, ctypes.c_int64, _dp]
     L.pibm_profile_steps.restype = ctypes.c_int
     L.pibm_destroy.argtypes = [vp]

@@ -597,8 +597,10 @@ State rebase_state(const State& s, const void* ws, void* tape) {
   }
   P.xr = rebase(Q.xr, a, b);
   P.cr = rebase(Q.cr, a, b);
-  P.xs = rebase(Q.xs, a, b);
-  P.cs = rebase(Q.cs, a, b);
+  for (int i = 0; i < 2; ++i) {
+    P.xs[i] = rebase(Q.xs[i], a, b);
+    P.cs[i] = rebase(Q.cs[i], a, b);
+  }
   P.g = rebase(Q.g, a, b);
   P.Fc = rebase(Q.Fc, a, b);
   P.rl = rebase(Q.rl, a, b);
@@ -628,7 +630,7 @@ cudaError_t adjoint_step(const State& T, AdjArgs A, double* gbar, double* fbar, 
   A.rad = T.p.rad[cur];
   A.gw = T.p.gw[cur];
   A.pid = T.p.pid[cur];
-  A.cs = T.p.cs;
+  A.cs = T.p.cs[cur];
   A.start = T.p.bin_cnt;
   A.mom = (const double*)T.mom;
   cudaError_t e = cudaMemsetAsync(A.rjbar, 0, sizeof(double) * 4 * g.pitch, st);
@@ -683,7 +685,7 @@ int settling_gradient(const pibm_config* cfg_in, int64_t nsteps, int64_t K, void
   if (cfg_in->n_particles < 1) return PIBM_EINVAL;
   if (cfg_in->precision != PIBM_FP64 || cfg_in->coupling != PIBM_IMPLICIT ||
       cfg_in->interp != PIBM_INTERP_DELTA || cfg_in->dem_model != PIBM_DEM_LINEAR ||
-      cfg_in->dem_substeps > 1)
+      cfg_in->dem_substeps > 1 || cfg_in->rebin_every > 1)
     return PIBM_ENOTSUP;
   pibm_config cfg = *cfg_in;
   cfg.deterministic = 1;  // replayed stretches reproduce the forward run bit for bit

@@ -26,6 +26,10 @@ struct pibm_t {
   double* out_dev;         // small device scratch for reductions
   int kernels_per_step;
   int debug_sync;          // synchronise after every phase (PIBM_DEBUG_SYNC=1)
+  int since_rebin;         // steps since the cell list was last rebuilt (0: rebuild next)
+  int64_t launches;        // kernels launched by pibm_step so far
+  int64_t graph_kernels;   // kernels in one replay of the step graphs
+  int graph_steps;         // steps in one replay of the step graphs
 };
 
 namespace {
@@ -103,6 +107,8 @@ int validate(const pibm_config* c) {
       return PIBM_EINVAL;
   }
   if (c->dem_substeps < 0 || c->dem_substeps > 4096) return PIBM_EINVAL;
+  if (c->rebin_every < 0 || c->rebin_every > 100000) return PIBM_EINVAL;
+  if (c->rebin_every > 1 && c->dem_substeps > 1) return PIBM_ENOTSUP;
   if (c->n_particles > 0) {
     if (!c->x0 || !c->diameter || !c->density_ratio) return PIBM_EINVAL;
     for (int k = 0; k < d; ++k)  // contact and spreading stencils must not alias
@@ -165,8 +171,8 @@ Layout layout(const pibm_config* c) {
   L.tw = take(c->deterministic ? sizeof(double) * 12 * np : 0);
   L.xr = take(sizeof(float4) * np);
   L.cr = take(sizeof(int4) * np);
-  L.xs = take(sizeof(float4) * np);
-  L.cs = take(sizeof(int4) * np);
+  L.xs = take(2 * align_up(sizeof(float4) * np));
+  L.cs = take(2 * align_up(sizeof(int4) * np));
   L.g = take(sizeof(double) * d * np);
   L.Fc = take(sizeof(double) * d * np);
   L.key = take(sizeof(unsigned) * np);
@@ -205,33 +211,59 @@ void record_error(const char* what, cudaError_t e) {
     if (h->debug_sync) CK(cudaStreamSynchronize(st));      \
   } while (0)
 
-int enqueue_step(pibm_t* h, cudaStream_t st) {
+// One step: the cell list (when due), contacts, coupling, collision. nk
+// receives the number of kernels launched.
+int enqueue_step(pibm_t* h, cudaStream_t st, int* nk_out) {
   State& s = h->s;
   int nk = 0;
-  PHASE(launch_bin(s, st, &nk));
+  const bool rebuild = h->since_rebin == 0;
+  if (rebuild) PHASE(launch_bin(s, st, &nk));
   PHASE(launch_contacts(s, st, &nk));
   PHASE(launch_couple(s, st, &nk));
   PHASE(launch_collide_stream(s, st));
   nk += 1;
   s.cur ^= 1;
-  h->kernels_per_step = nk;
+  h->since_rebin = (h->since_rebin + 1) % s.phy.rebin;
+  if (rebuild) h->kernels_per_step = nk;
+  if (nk_out) *nk_out = nk;
   return PIBM_OK;
 }
 
+// Steps in one replay of the step graphs: a whole number of cell-list rebuild
+// periods that is even, so that the buffers and the rebuild phase both return
+// to where they started.
+int graph_length(const pibm_t* h) {
+  const int r = h->s.phy.rebin;
+  return r % 2 == 0 ? r : 2 * r;
+}
+
 int build_graph(pibm_t* h, int parity) {
-  // Capture two steps starting from buffer parity `parity`; after two steps the
-  // buffers are back where they started, so the graph can be replayed.
+  // Capture graph_length() steps starting from buffer parity `parity` with a
+  // cell-list rebuild due; afterwards the buffers and the rebuild phase are back
+  // where they started, so the graph can be replayed.
   cudaGraph_t g = nullptr;
-  int saved = h->s.cur;
+  const int saved = h->s.cur, saved_r = h->since_rebin, saved_k = h->kernels_per_step;
   h->s.cur = parity;
+  h->since_rebin = 0;
   if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     h->s.cur = saved;
+    h->since_rebin = saved_r;
     return PIBM_ECUDA;
   }
-  int rc = enqueue_step(h, h->cap);
-  if (rc == PIBM_OK) rc = enqueue_step(h, h->cap);
+  int rc = PIBM_OK;
+  int64_t total = 0;
+  const int len = graph_length(h);
+  for (int i = 0; i < len && rc == PIBM_OK; ++i) {
+    int nk = 0;
+    rc = enqueue_step(h, h->cap, &nk);
+    total += nk;
+  }
   cudaError_t e = cudaStreamEndCapture(h->cap, &g);
   h->s.cur = saved;
+  h->since_rebin = saved_r;
+  h->kernels_per_step = saved_k > 0 ? saved_k : h->kernels_per_step;
+  h->graph_kernels = total;
+  h->graph_steps = len;
   if (rc != PIBM_OK || e != cudaSuccess || !g) {
     if (g) cudaGraphDestroy(g);
     cudaGetLastError();
@@ -379,6 +411,7 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
     s.phy.hz_damp = 2.0 * sqrt(5.0 / 6.0) * s.phy.beta;
   }
   s.phy.substeps = cfg->dem_substeps > 1 ? cfg->dem_substeps : 1;
+  s.phy.rebin = cfg->rebin_every > 1 ? cfg->rebin_every : 1;
   {
     double dmax = 0.0;
     for (long long p = 0; p < cfg->n_particles; ++p) dmax = fmax(dmax, cfg->diameter[p]);
@@ -416,8 +449,10 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
   }
   P.xr = (float4*)(base + L.xr);
   P.cr = (int4*)(base + L.cr);
-  P.xs = (float4*)(base + L.xs);
-  P.cs = (int4*)(base + L.cs);
+  for (int b = 0; b < 2; ++b) {
+    P.xs[b] = (float4*)(base + L.xs + b * align_up(sizeof(float4) * np));
+    P.cs[b] = (int4*)(base + L.cs + b * align_up(sizeof(int4) * np));
+  }
   P.g = (double*)(base + L.g);
   P.rl = (double*)(base + L.rl);
   P.jl = (double*)(base + L.jl);
@@ -522,18 +557,22 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
 int pibm_step(pibm_t* h, int64_t nsteps) {
   if (!h || nsteps < 0) return PIBM_EINVAL;
   DeviceGuard guard(h->device);
+  const int len = graph_length(h);
   while (nsteps > 0) {
-    if (nsteps >= 2 && !h->graph_failed) {
+    if (h->since_rebin == 0 && nsteps >= len && !h->graph_failed) {
       const int par = h->s.cur;
       if (!h->graph[par] && build_graph(h, par) != PIBM_OK) {
         h->graph_failed = 1;
         continue;
       }
       CK(cudaGraphLaunch(h->graph[par], h->stream));
-      nsteps -= 2;  // two toggles leave s.cur unchanged
+      nsteps -= len;  // an even number of toggles leaves s.cur unchanged
+      h->launches += h->graph_kernels;
     } else {
-      int rc = enqueue_step(h, h->stream);
+      int nk = 0;
+      int rc = enqueue_step(h, h->stream, &nk);
       if (rc != PIBM_OK) return rc;
+      h->launches += nk;
       nsteps -= 1;
     }
   }
@@ -652,6 +691,12 @@ int pibm_status(pibm_t* h) {
 
 int pibm_kernels_per_step(pibm_t* h) { return h ? h->kernels_per_step : 0; }
 
+int pibm_launch_count(pibm_t* h, int64_t* count) {
+  if (!h || !count) return PIBM_EINVAL;
+  *count = h->launches;
+  return PIBM_OK;
+}
+
 int pibm_autotune(pibm_t* h, int* block_xy) {
   if (!h) return PIBM_EINVAL;
   DeviceGuard guard(h->device);
@@ -765,8 +810,8 @@ static int ensemble_capture(pibm_ensemble_t* e) {
       break;
     }
     const int saved = m->s.cur;
-    rc = enqueue_step(m, ln);
-    if (rc == PIBM_OK) rc = enqueue_step(m, ln);
+    rc = enqueue_step(m, ln, nullptr);
+    if (rc == PIBM_OK) rc = enqueue_step(m, ln, nullptr);
     m->s.cur = saved;
     cudaEvent_t join = ev();
     if (rc == PIBM_OK && (!join || cudaEventRecord(join, ln) != cudaSuccess ||
@@ -798,6 +843,7 @@ int pibm_ensemble_create(pibm_t* const* members, int count, void* stream, pibm_e
   int dev = -1;
   for (int i = 0; i < count; ++i) {
     if (!members[i]) return PIBM_EINVAL;
+    if (members[i]->s.phy.rebin > 1) return PIBM_ENOTSUP;  // members rebuild every step
     if (i == 0) dev = members[i]->device;
     if (members[i]->device != dev) return PIBM_EINVAL;
     for (int j = 0; j < i; ++j)
@@ -850,7 +896,7 @@ int pibm_ensemble_step(pibm_ensemble_t* e, int64_t nsteps) {
       nsteps -= 2;
     } else {
       for (pibm_t* m : e->members) {
-        int rc = enqueue_step(m, e->stream);
+        int rc = enqueue_step(m, e->stream, nullptr);
         if (rc != PIBM_OK) return rc;
       }
       nsteps -= 1;
@@ -899,7 +945,10 @@ int pibm_profile_steps(pibm_t* h, int64_t nsteps, double* phase_ms) {
     if (cudaEventRecord(ev[0], st) != cudaSuccess) rc = PIBM_ECUDA;
     for (int64_t i = 0; i < nsteps && rc == PIBM_OK; ++i) {
       cudaEvent_t* e = &ev[NP * i + 1];
-      if (launch_bin(s, st, &nk) != cudaSuccess || cudaEventRecord(e[0], st) != cudaSuccess ||
+      const bool rebuild = h->since_rebin == 0;
+      h->since_rebin = (h->since_rebin + 1) % s.phy.rebin;
+      if ((rebuild && launch_bin(s, st, &nk) != cudaSuccess) ||
+          cudaEventRecord(e[0], st) != cudaSuccess ||
           launch_contacts(s, st, &nk) != cudaSuccess ||
           cudaEventRecord(e[1], st) != cudaSuccess ||
           launch_couple(s, st, &nk) != cudaSuccess || cudaEventRecord(e[2], st) != cudaSuccess ||

@@ -393,6 +393,9 @@ struct CoupleArgs {
   unsigned* pidn;
   const float4* xs;     // [np] FP32 in-cell position and radius of step n, sorted order
   const int4* cs;       // [np] cell (x, y, z) and storage position, sorted order
+  float4* xsn;          // the same records for step n + 1 when the cell list is kept
+  int4* csn;
+  int keep_cells;       // 1: the next step keeps the cell list (write xsn, csn; skin check)
   float xf_margin;      // bound on the FP32 rounding error of a distance
   double* gout;      // [d][np] by slot
   double* Fcout;     // [d][np] by slot
@@ -871,8 +874,12 @@ __device__ __forceinline__ void move_constants(const CoupleArgs& A, unsigned p, 
 // and returns A_p g in amp. FP64 mode solves the update in FP64. The
 // FP32-storage modes (whose rho_l, j_l come from FP32 moments) form the velocity
 // increment U' - U and g in FP32 and add the increment to the FP64 state.
+// When the next step keeps the cell list, also writes the particle's sorted
+// record for it (same cell, offset of the new position from that cell) and
+// checks that the particle stays within the skin of that cell.
 template <int D, class St, typename FT>
 __device__ __forceinline__ void advance_particle(const CoupleArgs& A, long long sl, unsigned p,
+                                                 const int4& mc, const float4& mf,
                                                  const double (&X)[3], const double (&U)[3],
                                                  const double (&Fc)[3], typename St::R rs,
                                                  const typename St::R (&js)[3], FT (&amp)[3]) {
@@ -936,15 +943,29 @@ __device__ __forceinline__ void advance_particle(const CoupleArgs& A, long long 
       A.gout[k * np + sl] = (double)gg;
     }
   }
+  const int cell[3] = {mc.x, mc.y, mc.z};
+  float off[3] = {0.f, 0.f, 0.f};
+  bool far = false;
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     const double xn = advance_axis(X[k] + Un[k], g.n[k], g.periodic[k], esc);
     bad |= not_finite_bits(xn) || not_finite_bits(Un[k]);
     A.Xn[k * np + sl] = xn;
     A.Un[k * np + sl] = Un[k];
+    if (A.keep_cells) {
+      // distance from the cell centre, minimum image on periodic axes
+      const double dc = min_image(xn - ((double)cell[k] + 0.5), g.n[k], g.periodic[k]);
+      far |= !(fabs(dc) <= 0.5 + A.ph.skin);
+      off[k] = (float)(dc + 0.5);
+    }
   }
   if (bad) atomicOr(A.err, ERR_PARTICLE_NONFINITE);
   if (esc) atomicOr(A.err, ERR_ESCAPED);
+  if (A.keep_cells) {
+    if (far) atomicOr(A.err, ERR_SKIN);
+    A.csn[sl] = make_int4(mc.x, mc.y, mc.z, (int)sl);
+    A.xsn[sl] = make_float4(off[0], off[1], off[2], mf.w);
+  }
   move_constants(A, p, sl);
 }
 
@@ -994,7 +1015,7 @@ __global__ void __launch_bounds__(256, (Lattice<Q>::D == 2 && sizeof(typename St
     gather_moments<D, WI, R>(A, tx, ty, tz, rs, js);
 
     // --- particle update (Eq. 13) and force density (Eqs. 6-7) ---
-    advance_particle<D, St, FT>(A, sl, p, X, U, Fc, rs, js, amp);
+    advance_particle<D, St, FT>(A, sl, p, mc, mf, X, U, Fc, rs, js, amp);
   }
 
   // --- spreading (Eq. 9) with the delta kernel ---
@@ -1134,22 +1155,22 @@ __global__ void __launch_bounds__(256) k_sub_spread(CoupleArgs A) {
 // Deterministic spreading: every cell gathers, in a fixed order (neighbour cells
 // by ascending z, y, x offset; particles by storage position inside a cell), the
 // A_p g w of every particle whose stencil covers it, with the taps the coupling
-// kernel kept at each slot (A_p by storage position, g and taps by slot).
+// kernel kept at each slot (A_p, g and taps by slot). R: the search reach in
+// cells around each bin, the stencil's (1 for 2 taps, 2 for 4) plus one when the
+// cell list is kept across steps (particles within half a cell of their bin).
 // Writes every cell of F.
-template <int D, int W, typename FT>
+template <int D, int W, int R, typename FT>
 __global__ void __launch_bounds__(256) k_spread_gather(Geometry g, BinMap bm, long long np,
                                                        const int* __restrict__ ti,
                                                        const double* __restrict__ tw,
                                                        const double* __restrict__ Ap,
                                                        const double* __restrict__ gin,
-                                                       const unsigned* __restrict__ perm,
                                                        const unsigned* __restrict__ start,
                                                        FT* __restrict__ F) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x >= g.n[0] || y >= g.n[1]) return;
-  constexpr int R = (W == 2) ? 1 : 2;
   FT acc[3] = {FT(0), FT(0), FT(0)};
   const int cell[3] = {x, y, z};
 #pragma unroll 1
@@ -1179,7 +1200,6 @@ __global__ void __launch_bounds__(256) k_spread_gather(Geometry g, BinMap bm, lo
         if (one ? i > 0 : !ok[i]) continue;
         const unsigned lo = start[b[i]], hi = start[one ? b[NX - 1] + 1 : b[i] + 1];
         for (unsigned sl = lo; sl < hi; ++sl) {
-          const unsigned p = perm[sl];
           FT wt = FT(1);
 #pragma unroll
           for (int k = 0; k < D; ++k) {
@@ -1191,7 +1211,7 @@ __global__ void __launch_bounds__(256) k_spread_gather(Geometry g, BinMap bm, lo
             wt *= wk;
           }
           if (wt == FT(0)) continue;
-          const double a = Ap[p];
+          const double a = Ap[sl];
 #pragma unroll
           for (int k = 0; k < D; ++k) acc[k] += (FT)(a * gin[k * np + sl]) * wt;
         }
@@ -1315,12 +1335,12 @@ cudaError_t launch_bin(const State& s, cudaStream_t st, int* nk) {
   k_scan_top<<<1, SCAN_THREADS, 0, st>>>(P.block_sums, P.scan_blocks);
   k_scan_down<<<P.scan_blocks, SCAN_THREADS, 0, st>>>(P.bin_cnt, n, P.block_sums);
   k_bin_scatter<<<blocks_for(P.np, 256), 256, 0, st>>>(P.key, P.rank, P.bin_cnt, P.np, P.xr,
-                                                       P.cr, P.perm, P.xs, P.cs);
+                                                       P.cr, P.perm, P.xs[s.cur], P.cs[s.cur]);
   if (nk) *nk += 5;
   if (s.deterministic) {
     // bins in storage order: every sum over a bin then runs in a fixed order
     k_bin_sort<<<blocks_for(P.np, 256), 256, 0, st>>>(P.key, P.rank, P.bin_cnt, P.np, P.xr,
-                                                      P.cr, P.perm, P.xs, P.cs);
+                                                      P.cr, P.perm, P.xs[s.cur], P.cs[s.cur]);
     if (nk) *nk += 1;
   }
   return cudaGetLastError();
@@ -1353,8 +1373,11 @@ CoupleArgs couple_args(const State& s) {
   A.gwn = P.gw[n];
   A.cfn = P.cf[n];
   A.pidn = P.pid[n];
-  A.xs = P.xs;
-  A.cs = P.cs;
+  A.xs = P.xs[c];
+  A.cs = P.cs[c];
+  A.xsn = P.xs[n];
+  A.csn = P.cs[n];
+  A.keep_cells = s.phy.rebin > 1;
   // in-cell offsets are exact to 2^-24 and whole-cell differences exactly so
   A.xf_margin = 1e-5f;
   A.gout = P.g;
@@ -1420,8 +1443,15 @@ cudaError_t couple_t(const State& s, cudaStream_t st, int* nk) {
     int bx = g.n[0] <= 32 ? 32 : (g.n[0] <= 64 ? 64 : 128);
     dim3 blk(bx, 256 / bx, 1);
     dim3 grd((g.n[0] + blk.x - 1) / blk.x, (g.n[1] + blk.y - 1) / blk.y, g.n[2]);
-    k_spread_gather<D, W, FT><<<grd, blk, 0, st>>>(g, P.bm, P.np, P.ti, P.tw, P.Ap[s.cur], P.g,
-                                                   P.perm, P.bin_cnt, (FT*)s.F);
+    constexpr int R0 = W == 2 ? 1 : 2;
+    if (s.phy.rebin > 1)
+      k_spread_gather<D, W, R0 + 1, FT><<<grd, blk, 0, st>>>(g, P.bm, P.np, P.ti, P.tw,
+                                                             P.Ap[1 - s.cur], P.g, P.bin_cnt,
+                                                             (FT*)s.F);
+    else
+      k_spread_gather<D, W, R0, FT><<<grd, blk, 0, st>>>(g, P.bm, P.np, P.ti, P.tw,
+                                                         P.Ap[1 - s.cur], P.g, P.bin_cnt,
+                                                         (FT*)s.F);
     if (nk) *nk += 1;
   }
   return cudaGetLastError();

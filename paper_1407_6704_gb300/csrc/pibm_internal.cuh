@@ -232,7 +232,9 @@ struct Physics {
   double Epp, Epw;        // Hertz: effective modulus particle-particle, particle-wall
   double hz_damp;         // Hertz: 2 sqrt(5/6) beta
   int substeps;           // DEM sub-steps per fluid step (>= 1)
-  double skin;            // largest displacement within a sub-cycled step, (1 - d_max) / 2
+  double skin;            // largest displacement allowed away from the cell of the last
+                          // rebuild (or the step start when sub-cycling): (1 - d_max) / 2
+  int rebin;              // cell-list rebuild period in steps (>= 1)
 };
 
 // Tile of lattice cells handled by one CTA of the particle kernel.
@@ -270,8 +272,12 @@ struct Particles {
   unsigned* pid[2];  // user index of the particle at each storage position
   float4* xr;     // [np] FP32 in-cell position and radius by storage position (binning)
   int4* cr;       // [np] cell (x, y, z) and storage position (binning)
-  float4* xs;     // [np] xr in sorted (slot) order
-  int4* cs;       // [np] cr in sorted (slot) order
+  // sorted records by slot, double-buffered by state parity: written by the
+  // cell-list scatter for the current state, or by the coupling kernel of the
+  // previous step when the cell list is kept (cell of the last rebuild, offset
+  // of the current position from it)
+  float4* xs[2];  // FP32 position inside the cell and radius
+  int4* cs[2];    // cell (x, y, z) and storage position
   double* g;      // [d][np] force density of the last step (Eq. 7), by slot of that step
   double* Fc;     // [d][np] contact force of the last step, by slot of that step
   // DEM sub-cycling scratch, by slot (allocated when substeps > 1)

@@ -44,11 +44,12 @@ class Pibm:
                  precision="fp64", deterministic=False, kn=1e-2, restitution=0.9, x0=None,
                  u0=None, diameter=None, density_ratio=None, f0=None, device=None, stream=None,
                  interp="delta", contact="linear", young=1.0, poisson=0.3, wall_young=None,
-                 wall_poisson=None, substeps=1):
+                 wall_poisson=None, substeps=1, rebin_every=1):
         """interp: "delta" (the spreading kernel) or "lagrange4" (Eq. 5);
         contact: "linear" (kn) or "hertz" (Eq. 15 with young/poisson of the
         particles and of the walls, default the particles'); both use the
-        restitution coefficient; substeps: DEM sub-steps per fluid step."""
+        restitution coefficient; substeps: DEM sub-steps per fluid step;
+        rebin_every: cell-list rebuild period in steps (skin-checked)."""
         import torch
 
         self._torch = torch
@@ -80,7 +81,8 @@ class Pibm:
             {"delta": _lib.PIBM_INTERP_DELTA, "lagrange4": _lib.PIBM_INTERP_LAGRANGE4}[interp],
             {"linear": _lib.PIBM_DEM_LINEAR, "hertz": _lib.PIBM_DEM_HERTZ}[contact],
             float(young), float(poisson), float(wall_young or 0.0),
-            float(poisson if wall_poisson is None else wall_poisson), int(substeps))
+            float(poisson if wall_poisson is None else wall_poisson), int(substeps),
+            int(rebin_every))
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
             else torch.device(device)
         nbytes = ctypes.c_size_t()
@@ -122,6 +124,13 @@ class Pibm:
     @property
     def kernels_per_step(self):
         return self._L.pibm_kernels_per_step(self._h)
+
+    @property
+    def launch_count(self):
+        """Kernels launched by step() on this handle so far."""
+        n = ctypes.c_int64()
+        check(self._L.pibm_launch_count(self._h, ctypes.byref(n)), "pibm_launch_count")
+        return n.value
 
     # --- read-back -----------------------------------------------------------------
     def forces(self):

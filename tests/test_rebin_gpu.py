@@ -1,0 +1,125 @@
+"""Cell list kept across steps (``rebin_every`` > 1): between rebuilds the
+contact search and the ordered spreading use the bins of the last rebuild, and
+the coupling kernel carries each particle's record (cell of the rebuild, offset
+of the current position from it). Every touching pair is still found while each
+particle stays within (1 - d_max) / 2 of its rebuild cell, which the device
+checks. The results are the oracle's, at the FP64 bar, like every-step
+rebuilding.
+"""
+import numpy as np
+import pytest
+
+from tests.test_parity_gpu import LAT, TOL, make_case, rel_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    from paper_1407_6704_gb300 import build
+
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    build.build()
+
+
+def _run(c, steps, precision="fp64", deterministic=False, rebin=1, chunks=None):
+    from oracle.oracle import Oracle
+    from paper_1407_6704_gb300.pibm import Pibm
+
+    kw = dict(delta_width=c["width"], gravity=c["gravity"], kn=c["kn"], restitution=c["e"],
+              x0=c["X"], u0=c["U"], diameter=c["D"], density_ratio=c["R"], f0=c["f0"])
+    ref = Oracle(c["q"], c["n"], c["periodic"], c["tau"], implicit_drag=c["implicit"], **kw)
+    ref.step(steps)
+    with Pibm(LAT[c["q"]], c["n"], c["periodic"], c["tau"], implicit=c["implicit"],
+              precision=precision, deterministic=deterministic, rebin_every=rebin, **kw) as sim:
+        for k in (chunks or [steps]):
+            sim.step(k)
+        got = sim.read("pop", "rho", "j", "x", "u")
+        got["f_fpi"], got["f_c"] = sim.forces()
+        got["status"] = sim.status()
+        got["launches"] = sim.launch_count
+        got["kps"] = sim.kernels_per_step
+    return got, ref
+
+
+def _dense(q, n, seed, npart, periodic=None):
+    c = make_case(q=q, n=n, periodic=periodic or (0,) * len(n), tau=0.7, width=4, npart=npart,
+                  seed=seed, dia=(0.5, 0.8), rr=2.0, band=(0.25, 0.95), u_scale=2e-3, e=0.8,
+                  f0_eps=1e-3)
+    centre = np.array(n, dtype=float) / 2
+    c["X"] = centre + 0.85 * (c["X"] - centre)
+    return c
+
+
+def _check(got, ref, X0, tol=1e-10):
+    assert got["status"] == 0
+    e = rel_errors(got, ref, X0)
+    bad = {k: v for k, v in e.items() if not v <= TOL.get(k, tol)}
+    assert not bad, (bad, e)
+    return e
+
+
+@pytest.mark.parametrize("rebin", [5, 8])
+def test_kept_cell_list_2d_parity(rebin):
+    """Squeezed 2D cloud with contacts, walls and a periodic axis; 67 steps in
+    chunks so that graph replays and single steps interleave."""
+    c = _dense(9, (26, 22), 81, 180, periodic=(1, 0))
+    got, ref = _run(c, 67, rebin=rebin, chunks=[1, 30, 3, 33])
+    assert np.count_nonzero(np.abs(ref.Fc).sum(1)) > 10
+    print("rebin", rebin, _check(got, ref, c["X"]))
+
+
+def test_kept_cell_list_3d_parity():
+    c = _dense(19, (12, 11, 13), 82, 120)
+    got, ref = _run(c, 40, rebin=6)
+    assert np.count_nonzero(np.abs(ref.Fc).sum(1)) > 5
+    print("rebin 3d", _check(got, ref, c["X"]))
+
+
+def test_kept_cell_list_deterministic_repeat():
+    c = _dense(9, (24, 20), 83, 150)
+    a, ref = _run(c, 45, deterministic=True, rebin=4)
+    b, _ = _run(c, 45, deterministic=True, rebin=4)
+    _check(a, ref, c["X"])
+    for k in ("pop", "x", "u", "f_fpi", "f_c"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_kept_cell_list_fp32():
+    c = _dense(9, (40, 34), 84, 220)
+    got, ref = _run(c, 100, precision="fp32", rebin=10)
+    assert got["status"] == 0
+    rho_r, j_r = ref.moments()
+    ur, ug = j_r / rho_r, got["j"] / got["rho"]
+    l2 = np.sqrt(((ug - ur) ** 2).sum() / (ur ** 2).sum())
+    ex = np.abs(got["x"] - ref.X).max() / np.abs(ref.X - c["X"]).max()
+    eu = np.abs(got["u"] - ref.U).max() / np.abs(ref.U).max()
+    print("rebin fp32", l2, ex, eu)
+    assert l2 < 1e-4 and ex < 1e-4 and eu < 1e-4
+
+
+def test_launch_count_follows_the_rebuild_period():
+    """9 kernels on a rebuild step (binning 5, contacts, moments, coupling,
+    collide), 4 on the others; graph replays are counted like single steps."""
+    c = _dense(9, (24, 20), 85, 100)
+    got, _ = _run(c, 23, rebin=5, chunks=[3, 20])
+    rebuilds = len(range(0, 23, 5))
+    assert got["kps"] == 9
+    assert got["launches"] == 9 * rebuilds + 4 * (23 - rebuilds)
+
+
+def test_particle_leaving_its_cell_skin_is_reported():
+    from paper_1407_6704_gb300 import _lib
+    from paper_1407_6704_gb300.pibm import Pibm
+
+    # cell 16 at the rebuild; 0.1 per step passes 17.2 (the cell plus the 0.2-cell
+    # skin) at the 8th step, before the next rebuild
+    kw = dict(delta_width=4, x0=[[16.45, 16.0], [5.0, 5.0]], u0=[[0.1, 0.0], [0.0, 0.0]],
+              diameter=[0.6, 0.6], density_ratio=[50.0, 50.0])
+    with Pibm("d2q9", (32, 32), (1, 1), 0.8, rebin_every=10, **kw) as sim:
+        sim.step(10)
+        assert sim.status() == _lib.PIBM_EUNSTABLE
+    with Pibm("d2q9", (32, 32), (1, 1), 0.8, rebin_every=1, **kw) as sim:
+        sim.step(10)
+        assert sim.status() == 0
