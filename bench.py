@@ -210,9 +210,11 @@ def run_gpu(args, rank, world):
     results = {}
     clocks = None
     for prec in [args.precision] + [p for p in ("fp64", "fp32") if p != args.precision]:
-        sim = Pibm.from_workload(w, precision=prec, particles=(X, dia, rr))
+        sim = Pibm.from_workload(w, precision=prec, particles=(X, dia, rr),
+                                 rebin_every=args.rebin)
         stream = sim.stream
         sim.step(args.warmup)
+        n_launch0 = sim.launch_count
         # timed region: K steps through pibm_step (two-step CUDA graphs), CUDA
         # events on the handle's stream, barrier + synchronise on both sides
         e0 = torch.cuda.Event(enable_timing=True)
@@ -229,6 +231,7 @@ def run_gpu(args, rank, world):
             sampler.__exit__(None, None, None)
             clocks = sampler.summary()
         ms_graph = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+        launches = sim.launch_count - n_launch0
         # second region: the same steps launched phase by phase with CUDA events
         # between the phases (per-kernel durations for the roofline)
         barrier()
@@ -239,7 +242,7 @@ def run_gpu(args, rank, world):
         sim.close()
         results[prec] = dict(ms=ms_graph, ms_phased=max_over_ranks(ph["total"] / args.steps),
                              phases={k: v / args.steps for k, v in ph.items()}, status=st,
-                             kps=kps)
+                             kps=kps, launches=launches)
         if not args.both:
             break
 
@@ -249,7 +252,7 @@ def run_gpu(args, rank, world):
     prec = args.precision
     barrier()
     t0 = time.perf_counter()
-    sim = Pibm.from_workload(w, precision=prec, particles=(X, dia, rr))
+    sim = Pibm.from_workload(w, precision=prec, particles=(X, dia, rr), rebin_every=args.rebin)
     sim.step(args.steps)
     out = sim.read("x", "u")
     sim.close()
@@ -327,6 +330,7 @@ def run_gpu(args, rank, world):
         "config": {"workload": WORKLOAD_DESC, "lattice": "D2Q9", "n": list(w.n),
                    "particles": w.n_particles, "precision": prec,
                    "particle_state": "f64", "parallelism": f"replicas x{world}",
+                   "cell_list_rebuild_every": args.rebin,
                    "l2": "inputs larger than L2 (population buffers 2x151 MB f32 / 2x302 MB f64)"},
         "phases_ms_per_step": ph,
         "kernels": kern,
@@ -337,7 +341,7 @@ def run_gpu(args, rank, world):
                 "seconds": e2e_s, "h2d_bytes_per_step": h2d / args.steps,
                 "d2h_bytes_per_step": d2h / args.steps,
                 "note": "create from host arrays + K steps + read X, U to host"},
-        "gpu_launches": args.steps * r["kps"],
+        "gpu_launches": r["launches"],
         "status": r["status"],
     }
     for p, rr_ in results.items():
@@ -352,6 +356,8 @@ def run_gpu(args, rank, world):
             line[p]["collide_roofline"] = {"bound": "alu", "achieved": a,
                                            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                                            "frac": a / FP64_PEAK_TFLOPS}
+    if args.rebin > 1:
+        line["every_step_rebuild"] = every_step_bench(args, w, X, dia, rr)
     if args.ensemble:
         line["ensemble"] = ensemble_bench(args)
     if args.adjoint:
@@ -407,6 +413,29 @@ def ensemble_bench(args, k=None):
             "ms_per_step": ms_ens, "value": cells / (ms_ens * 1e-3) / 1e6, "unit": "MLUPS",
             "members_one_by_one_ms_per_step": ms_seq,
             "members_one_by_one_value": cells / (ms_seq * 1e-3) / 1e6, "status": status}
+
+
+def every_step_bench(args, w, X, dia, rr):
+    """The headline configuration with the cell list rebuilt every step, for
+    comparison (same physics; the rebuild period only changes the work)."""
+    import torch
+    from paper_1407_6704_gb300.pibm import Pibm
+
+    sim = Pibm.from_workload(w, precision=args.precision, particles=(X, dia, rr), rebin_every=1)
+    sim.step(args.warmup)
+    k = min(args.steps, 1000)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(sim.stream)
+    sim.step(k)
+    e1.record(sim.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / k
+    st = sim.status()
+    sim.close()
+    return {"steps": k, "ms_per_step": ms, "value": w.ncell / (ms * 1e-3) / 1e6,
+            "unit": "MLUPS", "status": st}
 
 
 def adjoint_bench(steps=500, K=50):
@@ -508,7 +537,8 @@ def run_profile_only(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
     w = preset(args.workload)
     X, dia, rr = workload_particles(w)
-    sim = Pibm.from_workload(w, precision=args.precision, particles=(X, dia, rr))
+    sim = Pibm.from_workload(w, precision=args.precision, particles=(X, dia, rr),
+                             rebin_every=args.rebin)
     sim.profile_steps(args.warmup)
     ph = sim.profile_steps(args.steps)
     print(json.dumps({"workload": args.workload, "precision": args.precision,
@@ -526,6 +556,8 @@ def main():
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--precision", choices=["fp32", "fp64", "fp16", "bf16"], default="fp32")
     ap.add_argument("--both", type=int, default=1, help="also time the other precision")
+    ap.add_argument("--rebin", type=int, default=10,
+                    help="cell-list rebuild period in steps (skin-checked on the device)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ensemble", type=int, default=1, help="also time the 64-member ensemble")
     ap.add_argument("--adjoint", type=int, default=1,
