@@ -39,7 +39,7 @@ constexpr size_t ALIGN = 256;
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-  size_t f, F, mom, red, err, out, X, U, rad, mass, Ap, buoy, gw, cf, pid, rl, jl, Fs, ti, tw, xr, cr, xs, cs, g, Fc, key, rank, perm, bin,
+  size_t f, F, mom, red, err, out, X, U, rad, mass, Ap, buoy, gw, cf, pid, rl, jl, Fs, ti, tw, nb, nbn, xr, cr, xs, cs, g, Fc, key, rank, perm, bin,
       bsum;
   size_t total;
 };
@@ -169,6 +169,9 @@ Layout layout(const pibm_config* c) {
   L.Fs = take(sub ? sizeof(double) * d * np : 0);
   L.ti = take(c->deterministic ? sizeof(int) * 12 * np : 0);
   L.tw = take(c->deterministic ? sizeof(double) * 12 * np : 0);
+  const bool keep = c->rebin_every > 1;
+  L.nb = take(keep ? sizeof(unsigned) * (d == 2 ? 24 : 64) * np : 0);
+  L.nbn = take(keep ? sizeof(int) * np : 0);
   L.xr = take(sizeof(float4) * np);
   L.cr = take(sizeof(int4) * np);
   L.xs = take(2 * align_up(sizeof(float4) * np));
@@ -218,6 +221,7 @@ int enqueue_step(pibm_t* h, cudaStream_t st, int* nk_out) {
   int nk = 0;
   const bool rebuild = h->since_rebin == 0;
   if (rebuild) PHASE(launch_bin(s, st, &nk));
+  s.nb_mode = rebuild ? 1 : 2;
   PHASE(launch_contacts(s, st, &nk));
   PHASE(launch_couple(s, st, &nk));
   PHASE(launch_collide_stream(s, st));
@@ -459,6 +463,9 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
   P.Fs = (double*)(base + L.Fs);
   P.ti = (int*)(base + L.ti);
   P.tw = (double*)(base + L.tw);
+  P.nb = (unsigned*)(base + L.nb);
+  P.nbn = (int*)(base + L.nbn);
+  P.nb_max = d == 2 ? 24 : 64;
   P.Fc = (double*)(base + L.Fc);
   P.key = (unsigned*)(base + L.key);
   P.rank = (unsigned*)(base + L.rank);
@@ -947,6 +954,7 @@ int pibm_profile_steps(pibm_t* h, int64_t nsteps, double* phase_ms) {
       cudaEvent_t* e = &ev[NP * i + 1];
       const bool rebuild = h->since_rebin == 0;
       h->since_rebin = (h->since_rebin + 1) % s.phy.rebin;
+      s.nb_mode = rebuild ? 1 : 2;
       if ((rebuild && launch_bin(s, st, &nk) != cudaSuccess) ||
           cudaEventRecord(e[0], st) != cudaSuccess ||
           launch_contacts(s, st, &nk) != cudaSuccess ||

@@ -396,6 +396,10 @@ struct CoupleArgs {
   float4* xsn;          // the same records for step n + 1 when the cell list is kept
   int4* csn;
   int keep_cells;       // 1: the next step keeps the cell list (write xsn, csn; skin check)
+  int nb_mode;          // contact candidates: 0 traverse, 1 traverse and record, 2 use the record
+  int nb_max;           // capacity of the candidate record per particle
+  unsigned* nb;         // [nb_max][np] candidate slots recorded at the last rebuild
+  int* nbn;             // [np] their number, -1 when they did not fit
   float xf_margin;      // bound on the FP32 rounding error of a distance
   double* gout;      // [d][np] by slot
   double* Fcout;     // [d][np] by slot
@@ -439,8 +443,11 @@ __device__ __forceinline__ double normal_force(const Physics& ph, double delta, 
 // restitution coefficient e. Candidates are first screened in FP32 with a
 // margin larger than the FP32 rounding of the positions (xf_margin), plus twice
 // the largest sub-step displacement, so only pairs that may overlap reach the
-// FP64 overlap test; the force itself is FP64. HZ selects the Hertz law.
-template <int D, bool SUB, bool HZ>
+// FP64 overlap test; the force itself is FP64. HZ selects the Hertz law. With a
+// kept cell list the traversal of a rebuild step records each particle's
+// candidates and the following steps take them from the record: the same
+// candidates in the same order, so the same sums.
+template <int D, bool SUB, bool HZ, int NB>
 __global__ void __launch_bounds__(256) k_contacts(CoupleArgs A) {
   const long long sl = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (sl >= A.np) return;
@@ -463,85 +470,104 @@ __global__ void __launch_bounds__(256) k_contacts(CoupleArgs A) {
   const float rpf = me.w;
   const int bc[3] = {mc.x, mc.y, mc.z};
   double Fc[3] = {0.0, 0.0, 0.0};
-#pragma unroll 1
-  for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz) {
-    int cz = bc[2] + oz;
-    if (D == 3 && !lattice_coord(cz, g.n[2], g.periodic[2])) continue;
-#pragma unroll 1
-    for (int oy = -1; oy <= 1; ++oy) {
-      int cy = bc[1] + oy;
-      if (!lattice_coord(cy, g.n[1], g.periodic[1])) continue;
-      // the cells x-1, x, x+1 of this row: one run of consecutive bins in the
-      // common case, else each in-domain cell on its own
-      unsigned b[3];
-      bool ok[3];
+  // the contact force of the candidate at slot s2
+  auto consider = [&](unsigned s2) {
+    const float4 o = A.xs[s2];
+    const int4 oc = A.cs[s2];
+    const float oq[3] = {o.x, o.y, o.z};
+    const int cq[3] = {oc.x, oc.y, oc.z};
+    float d2f = 0.f;
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        int cx = bc[0] + i - 1;
-        ok[i] = lattice_coord(cx, g.n[0], g.periodic[0]);
-        b[i] = ok[i] ? bin_index<D>(bm, cx, cy, cz) : 0u;
+    for (int k = 0; k < D; ++k) {
+      // whole cells apart (minimum image on periodic axes) plus the in-cell offsets
+      int dc = bc[k] - cq[k];
+      if (g.periodic[k]) {
+        if (2 * dc > g.n[k]) dc -= g.n[k];
+        if (2 * dc < -g.n[k]) dc += g.n[k];
       }
-      const bool one = ok[0] && ok[1] && ok[2] && b[1] == b[0] + 1 && b[2] == b[1] + 1;
-#pragma unroll 1
-      for (int r = 0; r < (one ? 1 : 3); ++r) {
-        const bool okr = one || (r == 0 ? ok[0] : (r == 1 ? ok[1] : ok[2]));
-        if (!okr) continue;
-        const unsigned br = r == 0 ? b[0] : (r == 1 ? b[1] : b[2]);
-        const unsigned lo = A.start[br], hi = A.start[one ? b[2] + 1 : br + 1];
-        if (hi > (unsigned)np || lo > hi) {
-          atomicOr(A.err, ERR_INDEX);
-          continue;
-        }
-        for (unsigned s2 = lo; s2 < hi; ++s2) {
-          if (s2 == (unsigned)sl) continue;
-          const float4 o = A.xs[s2];
-          const int4 oc = A.cs[s2];
-          const float oq[3] = {o.x, o.y, o.z};
-          const int cq[3] = {oc.x, oc.y, oc.z};
-          float d2f = 0.f;
+      const float s = (float)dc + (xp[k] - oq[k]);
+      d2f += s * s;
+    }
+    const float reach = rpf + o.w + mrg;
+    if (d2f > reach * reach) return;
+    const unsigned q = (unsigned)oc.w;
+    // FP64 overlap test and force
+    if (q >= (unsigned)np) {
+      atomicOr(A.err, ERR_INDEX);
+      return;
+    }
+    const unsigned ot_i = SUB ? s2 : q;
+    double s[3], d2 = 0.0;
 #pragma unroll
-          for (int k = 0; k < D; ++k) {
-            // whole cells apart (minimum image on periodic axes) plus the in-cell offsets
-            int dc = bc[k] - cq[k];
-            if (g.periodic[k]) {
-              if (2 * dc > g.n[k]) dc -= g.n[k];
-              if (2 * dc < -g.n[k]) dc += g.n[k];
-            }
-            const float s = (float)dc + (xp[k] - oq[k]);
-            d2f += s * s;
-          }
-          const float reach = rpf + o.w + mrg;
-          if (d2f > reach * reach) continue;
-          const unsigned q = (unsigned)oc.w;
-          // FP64 overlap test and force
-          if (q >= (unsigned)np) {
+    for (int k = 0; k < D; ++k) {
+      s[k] = min_image(Xat(k, me_i) - Xat(k, ot_i), g.n[k], g.periodic[k]);
+      d2 += s[k] * s[k];
+    }
+    const double dist = sqrt(d2);
+    const double rp = A.rad[p], rq = A.rad[q];
+    const double delta = rp + rq - dist;
+    if (!(delta > 0.0) || !(dist > 0.0)) return;
+    const double mp = A.mass[p], mq = A.mass[q];
+    const double meff = mp * mq / (mp + mq);
+    const double inv = 1.0 / dist;
+    double vn = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) vn += (Uat(k, me_i) - Uat(k, ot_i)) * (s[k] * inv);
+    const double mag =
+        normal_force<HZ>(A.ph, delta, vn, meff, HZ ? rp * rq / (rp + rq) : 0.0, A.ph.Epp);
+#pragma unroll
+    for (int k = 0; k < D; ++k) Fc[k] += mag * (s[k] * inv);
+  };
+  // NB: 0 traverse the cells, 1 traverse and record the candidates, 2 take the
+  // recorded candidates (traversing when they did not fit)
+  if (NB == 2 && A.nbn[sl] >= 0) {
+    // the candidates the traversal of the last rebuild recorded, in its order
+    const int cnt = A.nbn[sl];
+    for (int i = 0; i < cnt; ++i) consider(A.nb[(long long)i * np + sl]);
+  } else {
+    const bool rec = NB == 1;
+    int nrec = 0;
+#pragma unroll 1
+    for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz) {
+      int cz = bc[2] + oz;
+      if (D == 3 && !lattice_coord(cz, g.n[2], g.periodic[2])) continue;
+#pragma unroll 1
+      for (int oy = -1; oy <= 1; ++oy) {
+        int cy = bc[1] + oy;
+        if (!lattice_coord(cy, g.n[1], g.periodic[1])) continue;
+        // the cells x-1, x, x+1 of this row: one run of consecutive bins in the
+        // common case, else each in-domain cell on its own
+        unsigned b[3];
+        bool ok[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          int cx = bc[0] + i - 1;
+          ok[i] = lattice_coord(cx, g.n[0], g.periodic[0]);
+          b[i] = ok[i] ? bin_index<D>(bm, cx, cy, cz) : 0u;
+        }
+        const bool one = ok[0] && ok[1] && ok[2] && b[1] == b[0] + 1 && b[2] == b[1] + 1;
+#pragma unroll 1
+        for (int r = 0; r < (one ? 1 : 3); ++r) {
+          const bool okr = one || (r == 0 ? ok[0] : (r == 1 ? ok[1] : ok[2]));
+          if (!okr) continue;
+          const unsigned br = r == 0 ? b[0] : (r == 1 ? b[1] : b[2]);
+          const unsigned lo = A.start[br], hi = A.start[one ? b[2] + 1 : br + 1];
+          if (hi > (unsigned)np || lo > hi) {
             atomicOr(A.err, ERR_INDEX);
             continue;
           }
-          const unsigned ot_i = SUB ? s2 : q;
-          double s[3], d2 = 0.0;
-#pragma unroll
-          for (int k = 0; k < D; ++k) {
-            s[k] = min_image(Xat(k, me_i) - Xat(k, ot_i), g.n[k], g.periodic[k]);
-            d2 += s[k] * s[k];
+          for (unsigned s2 = lo; s2 < hi; ++s2) {
+            if (s2 == (unsigned)sl) continue;
+            if (rec) {
+              if (nrec < A.nb_max) A.nb[(long long)nrec * np + sl] = s2;
+              ++nrec;
+            }
+            consider(s2);
           }
-          const double dist = sqrt(d2);
-          const double rp = A.rad[p], rq = A.rad[q];
-          const double delta = rp + rq - dist;
-          if (!(delta > 0.0) || !(dist > 0.0)) continue;
-          const double mp = A.mass[p], mq = A.mass[q];
-          const double meff = mp * mq / (mp + mq);
-          const double inv = 1.0 / dist;
-          double vn = 0.0;
-#pragma unroll
-          for (int k = 0; k < D; ++k) vn += (Uat(k, me_i) - Uat(k, ot_i)) * (s[k] * inv);
-          const double mag = normal_force<HZ>(A.ph, delta, vn, meff, HZ ? rp * rq / (rp + rq) : 0.0,
-                                              A.ph.Epp);
-#pragma unroll
-          for (int k = 0; k < D; ++k) Fc[k] += mag * (s[k] * inv);
         }
       }
     }
+    if (rec) A.nbn[sl] = nrec <= A.nb_max ? nrec : -1;  // -1: traverse again
   }
 #pragma unroll
   for (int k = 0; k < D; ++k) {
@@ -1378,6 +1404,10 @@ CoupleArgs couple_args(const State& s) {
   A.xsn = P.xs[n];
   A.csn = P.cs[n];
   A.keep_cells = s.phy.rebin > 1;
+  A.nb_mode = s.phy.rebin > 1 ? s.nb_mode : 0;
+  A.nb_max = P.nb_max;
+  A.nb = P.nb;
+  A.nbn = P.nbn;
   // in-cell offsets are exact to 2^-24 and whole-cell differences exactly so
   A.xf_margin = 1e-5f;
   A.gout = P.g;
@@ -1426,9 +1456,9 @@ cudaError_t couple_t(const State& s, cudaStream_t st, int* nk) {
     const double h = 1.0 / (double)s.phy.substeps;
     for (int k = 0; k < s.phy.substeps; ++k) {
       if (s.phy.hertz)
-        k_contacts<D, true, true><<<pb, 256, 0, st>>>(A);
+        k_contacts<D, true, true, 0><<<pb, 256, 0, st>>>(A);
       else
-        k_contacts<D, true, false><<<pb, 256, 0, st>>>(A);
+        k_contacts<D, true, false, 0><<<pb, 256, 0, st>>>(A);
       k_substep<D><<<pb, 256, 0, st>>>(A, h);
     }
     n += 1 + 2 * s.phy.substeps;
@@ -1463,17 +1493,26 @@ cudaError_t couple_w(const State& s, cudaStream_t st, int* nk) {
 }
 }  // namespace
 
+namespace {
+template <int D, bool HZ>
+void contacts_nb(const CoupleArgs& A, unsigned pb, cudaStream_t st) {
+  if (A.nb_mode == 1) k_contacts<D, false, HZ, 1><<<pb, 256, 0, st>>>(A);
+  else if (A.nb_mode == 2) k_contacts<D, false, HZ, 2><<<pb, 256, 0, st>>>(A);
+  else k_contacts<D, false, HZ, 0><<<pb, 256, 0, st>>>(A);
+}
+}  // namespace
+
 cudaError_t launch_contacts(const State& s, cudaStream_t st, int* nk) {
   // with DEM sub-cycling the contacts run inside the particle phase, per sub-step
   if (s.p.np == 0 || s.phy.substeps > 1) return cudaSuccess;
   CoupleArgs A = couple_args(s);
   const unsigned pb = blocks_for(s.p.np, 256);
   if (s.geo.d == 2) {
-    if (s.phy.hertz) k_contacts<2, false, true><<<pb, 256, 0, st>>>(A);
-    else k_contacts<2, false, false><<<pb, 256, 0, st>>>(A);
+    if (s.phy.hertz) contacts_nb<2, true>(A, pb, st);
+    else contacts_nb<2, false>(A, pb, st);
   } else {
-    if (s.phy.hertz) k_contacts<3, false, true><<<pb, 256, 0, st>>>(A);
-    else k_contacts<3, false, false><<<pb, 256, 0, st>>>(A);
+    if (s.phy.hertz) contacts_nb<3, true>(A, pb, st);
+    else contacts_nb<3, false>(A, pb, st);
   }
   if (nk) *nk += 1;
   return cudaGetLastError();

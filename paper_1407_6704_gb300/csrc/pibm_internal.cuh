@@ -287,6 +287,10 @@ struct Particles {
   // ordered spreading (deterministic mode): each particle's spreading taps, by slot
   int* ti;        // [np][3][4] cell index per axis and node
   double* tw;     // [np][3][4] weight per axis and node
+  // kept cell list (rebin_every > 1): contact candidates recorded at the rebuild
+  unsigned* nb;   // [nb_max][np] candidate slots
+  int* nbn;       // [np] candidate count, -1 when more than nb_max
+  int nb_max;
   // cell list (bins = lattice cells)
   unsigned* key;      // [np] bin of each particle
   unsigned* rank;     // [np] arrival rank inside the bin
@@ -311,6 +315,7 @@ struct State {
   Particles p;
   int cur;        // index of the buffer holding the current f* / X / U
   int cblk[2];    // collide-stream block shape (x, y); 0 = built-in choice
+  int nb_mode;    // this step's contact search: 1 traverse and record candidates, 2 reuse them
 };
 
 // ---------------------------------------------------------------------------
