@@ -222,6 +222,9 @@ int enqueue_step(pibm_t* h, cudaStream_t st, int* nk_out) {
   const bool rebuild = h->since_rebin == 0;
   if (rebuild) PHASE(launch_bin(s, st, &nk));
   s.nb_mode = rebuild ? 1 : 2;
+  // between rebuilds the storage order holds, so from the second step after a
+  // rebuild the other buffer already holds the constants in that order
+  s.move_consts = h->since_rebin <= 1;
   PHASE(launch_contacts(s, st, &nk));
   PHASE(launch_couple(s, st, &nk));
   PHASE(launch_collide_stream(s, st));
@@ -953,6 +956,7 @@ int pibm_profile_steps(pibm_t* h, int64_t nsteps, double* phase_ms) {
     for (int64_t i = 0; i < nsteps && rc == PIBM_OK; ++i) {
       cudaEvent_t* e = &ev[NP * i + 1];
       const bool rebuild = h->since_rebin == 0;
+      s.move_consts = h->since_rebin <= 1;
       h->since_rebin = (h->since_rebin + 1) % s.phy.rebin;
       s.nb_mode = rebuild ? 1 : 2;
       if ((rebuild && launch_bin(s, st, &nk) != cudaSuccess) ||

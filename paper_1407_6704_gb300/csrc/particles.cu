@@ -397,6 +397,7 @@ struct CoupleArgs {
   int4* csn;
   int keep_cells;       // 1: the next step keeps the cell list (write xsn, csn; skin check)
   int nb_mode;          // contact candidates: 0 traverse, 1 traverse and record, 2 use the record
+  int move_consts;      // 0: the other buffer already holds the constants in this order
   int nb_max;           // capacity of the candidate record per particle
   unsigned* nb;         // [nb_max][np] candidate slots recorded at the last rebuild
   int* nbn;             // [np] their number, -1 when they did not fit
@@ -989,10 +990,11 @@ __device__ __forceinline__ void advance_particle(const CoupleArgs& A, long long 
   if (esc) atomicOr(A.err, ERR_ESCAPED);
   if (A.keep_cells) {
     if (far) atomicOr(A.err, ERR_SKIN);
-    A.csn[sl] = make_int4(mc.x, mc.y, mc.z, (int)sl);
+    // the cell and slot change only at a rebuild (written then and on the step after)
+    if (A.move_consts) A.csn[sl] = make_int4(mc.x, mc.y, mc.z, (int)sl);
     A.xsn[sl] = make_float4(off[0], off[1], off[2], mf.w);
   }
-  move_constants(A, p, sl);
+  if (A.move_consts) move_constants(A, p, sl);
 }
 
 // Particle coupling, one thread per particle in cell-sorted order: interpolate
@@ -1405,6 +1407,7 @@ CoupleArgs couple_args(const State& s) {
   A.csn = P.cs[n];
   A.keep_cells = s.phy.rebin > 1;
   A.nb_mode = s.phy.rebin > 1 ? s.nb_mode : 0;
+  A.move_consts = s.phy.rebin > 1 ? s.move_consts : 1;
   A.nb_max = P.nb_max;
   A.nb = P.nb;
   A.nbn = P.nbn;

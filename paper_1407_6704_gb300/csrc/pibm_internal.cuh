@@ -316,6 +316,8 @@ struct State {
   int cur;        // index of the buffer holding the current f* / X / U
   int cblk[2];    // collide-stream block shape (x, y); 0 = built-in choice
   int nb_mode;    // this step's contact search: 1 traverse and record candidates, 2 reuse them
+  int move_consts;  // 1: the coupling kernel moves the particles' constants to their slots
+                    // (needed unless the order held for the last two steps)
 };
 
 // ---------------------------------------------------------------------------
