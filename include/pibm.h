@@ -147,11 +147,13 @@ typedef struct pibm_config {
                           raises PIBM_EUNSTABLE. */
   int rebin_every;     /* rebuild the cell list every R steps (0 or 1: every step). In
                           between, the contact search and the ordered spreading use the
-                          bins of the last rebuild; this finds every touching pair as long
-                          as each particle stays within (1 - largest diameter) / 2 of the
-                          cell it had at the last rebuild, which is checked on the device
-                          every step (PIBM_EUNSTABLE when violated). Results equal those of
-                          R = 1 up to the summation order. Needs dem_substeps <= 1. */
+                          bins of the last rebuild and the contact candidates it recorded;
+                          this finds every touching pair as long as each particle stays
+                          within (1 - largest diameter) / 2 of the cell it had at the last
+                          rebuild and within (1 - largest diameter) / 4 of its position
+                          then, on every axis, which is checked on the device every step
+                          (PIBM_EUNSTABLE when violated). Results equal those of R = 1 up to
+                          the summation order. Needs dem_substeps <= 1. */
 } pibm_config;
 
 typedef struct pibm_t pibm_t; /* opaque handle owning the device state */

@@ -39,7 +39,7 @@ constexpr size_t ALIGN = 256;
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-  size_t f, F, mom, red, err, out, X, U, rad, mass, Ap, buoy, gw, cf, pid, rl, jl, Fs, ti, tw, nb, nbn, xr, cr, xs, cs, g, Fc, key, rank, perm, bin,
+  size_t f, F, mom, red, err, out, X, U, rad, mass, Ap, buoy, gw, cf, pid, rl, jl, Fs, ti, tw, nb, nbn, xs0, xr, cr, xs, cs, g, Fc, key, rank, perm, bin,
       bsum;
   size_t total;
 };
@@ -172,6 +172,7 @@ Layout layout(const pibm_config* c) {
   const bool keep = c->rebin_every > 1;
   L.nb = take(keep ? sizeof(unsigned) * (d == 2 ? 24 : 64) * np : 0);
   L.nbn = take(keep ? sizeof(int) * np : 0);
+  L.xs0 = take(keep ? sizeof(float4) * np : 0);
   L.xr = take(sizeof(float4) * np);
   L.cr = take(sizeof(int4) * np);
   L.xs = take(2 * align_up(sizeof(float4) * np));
@@ -423,6 +424,7 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
     double dmax = 0.0;
     for (long long p = 0; p < cfg->n_particles; ++p) dmax = fmax(dmax, cfg->diameter[p]);
     s.phy.skin = 0.5 * (1.0 - dmax);
+    s.phy.disp_skin = 0.25 * (1.0 - dmax);
   }
   s.precision = cfg->precision;
   s.deterministic = cfg->deterministic ? 1 : 0;
@@ -468,6 +470,7 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
   P.tw = (double*)(base + L.tw);
   P.nb = (unsigned*)(base + L.nb);
   P.nbn = (int*)(base + L.nbn);
+  P.xs0 = cfg->rebin_every > 1 ? (float4*)(base + L.xs0) : nullptr;
   P.nb_max = d == 2 ? 24 : 64;
   P.Fc = (double*)(base + L.Fc);
   P.key = (unsigned*)(base + L.key);

@@ -158,13 +158,14 @@ __global__ void k_bin_scatter(const unsigned* __restrict__ key, const unsigned* 
                               const unsigned* __restrict__ start, long long np,
                               const float4* __restrict__ xr, const int4* __restrict__ cr,
                               unsigned* __restrict__ perm, float4* __restrict__ xs,
-                              int4* __restrict__ cs) {
+                              int4* __restrict__ cs, float4* __restrict__ xs0) {
   long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= np) return;
   const unsigned sl = start[key[p]] + rank[p];
   perm[sl] = (unsigned)p;
   xs[sl] = xr[p];
   cs[sl] = cr[p];
+  if (xs0) xs0[sl] = xr[p];  // kept cell list: the offsets at the rebuild
 }
 
 // Deterministic mode: order every bin by storage position so that every sum over a
@@ -173,7 +174,7 @@ __global__ void k_bin_sort(const unsigned* __restrict__ key, const unsigned* __r
                            const unsigned* __restrict__ start, long long np,
                            const float4* __restrict__ xr, const int4* __restrict__ cr,
                            unsigned* __restrict__ perm, float4* __restrict__ xs,
-                           int4* __restrict__ cs) {
+                           int4* __restrict__ cs, float4* __restrict__ xs0) {
   long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= np || rank[p] != 0u) return;
   unsigned b = key[p];
@@ -190,6 +191,7 @@ __global__ void k_bin_sort(const unsigned* __restrict__ key, const unsigned* __r
   for (unsigned i = lo; i < hi; ++i) {
     xs[i] = xr[perm[i]];
     cs[i] = cr[perm[i]];
+    if (xs0) xs0[i] = xr[perm[i]];
   }
 }
 
@@ -396,6 +398,7 @@ struct CoupleArgs {
   float4* xsn;          // the same records for step n + 1 when the cell list is kept
   int4* csn;
   int keep_cells;       // 1: the next step keeps the cell list (write xsn, csn; skin check)
+  const float4* xs0;    // in-cell offsets at the last rebuild, by slot (kept cell list)
   int nb_mode;          // contact candidates: 0 traverse, 1 traverse and record, 2 use the record
   int move_consts;      // 0: the other buffer already holds the constants in this order
   int nb_max;           // capacity of the candidate record per particle
@@ -519,6 +522,28 @@ __global__ void __launch_bounds__(256) k_contacts(CoupleArgs A) {
 #pragma unroll
     for (int k = 0; k < D; ++k) Fc[k] += mag * (s[k] * inv);
   };
+  // At a rebuild, the candidates that can touch before the next one: every
+  // particle stays within disp_skin of its rebuild position on each axis, so a
+  // pair farther apart than r_i + r_j + 2 disp_skin sqrt(d) never touches.
+  auto near_at_rebuild = [&](unsigned s2) {
+    const float4 o = A.xs[s2];
+    const int4 oc = A.cs[s2];
+    const float oq[3] = {o.x, o.y, o.z};
+    const int cq[3] = {oc.x, oc.y, oc.z};
+    float d2f = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      int dc = bc[k] - cq[k];
+      if (g.periodic[k]) {
+        if (2 * dc > g.n[k]) dc -= g.n[k];
+        if (2 * dc < -g.n[k]) dc += g.n[k];
+      }
+      const float s = (float)dc + (xp[k] - oq[k]);
+      d2f += s * s;
+    }
+    const float reach = rpf + o.w + 2.f * (float)A.ph.disp_skin * sqrtf((float)D) + mrg;
+    return d2f <= reach * reach;
+  };
   // NB: 0 traverse the cells, 1 traverse and record the candidates, 2 take the
   // recorded candidates (traversing when they did not fit)
   if (NB == 2 && A.nbn[sl] >= 0) {
@@ -559,7 +584,7 @@ __global__ void __launch_bounds__(256) k_contacts(CoupleArgs A) {
           }
           for (unsigned s2 = lo; s2 < hi; ++s2) {
             if (s2 == (unsigned)sl) continue;
-            if (rec) {
+            if (rec && near_at_rebuild(s2)) {
               if (nrec < A.nb_max) A.nb[(long long)nrec * np + sl] = s2;
               ++nrec;
             }
@@ -989,6 +1014,11 @@ __device__ __forceinline__ void advance_particle(const CoupleArgs& A, long long 
   if (bad) atomicOr(A.err, ERR_PARTICLE_NONFINITE);
   if (esc) atomicOr(A.err, ERR_ESCAPED);
   if (A.keep_cells) {
+    // and within disp_skin of its position at the rebuild (the recorded candidates)
+    const float4 o0 = A.xs0[sl];
+    const float q0[3] = {o0.x, o0.y, o0.z};
+#pragma unroll
+    for (int k = 0; k < D; ++k) far |= !(fabsf(off[k] - q0[k]) <= (float)A.ph.disp_skin);
     if (far) atomicOr(A.err, ERR_SKIN);
     // the cell and slot change only at a rebuild (written then and on the step after)
     if (A.move_consts) A.csn[sl] = make_int4(mc.x, mc.y, mc.z, (int)sl);
@@ -1363,12 +1393,12 @@ cudaError_t launch_bin(const State& s, cudaStream_t st, int* nk) {
   k_scan_top<<<1, SCAN_THREADS, 0, st>>>(P.block_sums, P.scan_blocks);
   k_scan_down<<<P.scan_blocks, SCAN_THREADS, 0, st>>>(P.bin_cnt, n, P.block_sums);
   k_bin_scatter<<<blocks_for(P.np, 256), 256, 0, st>>>(P.key, P.rank, P.bin_cnt, P.np, P.xr,
-                                                       P.cr, P.perm, P.xs[s.cur], P.cs[s.cur]);
+                                                       P.cr, P.perm, P.xs[s.cur], P.cs[s.cur], P.xs0);
   if (nk) *nk += 5;
   if (s.deterministic) {
     // bins in storage order: every sum over a bin then runs in a fixed order
     k_bin_sort<<<blocks_for(P.np, 256), 256, 0, st>>>(P.key, P.rank, P.bin_cnt, P.np, P.xr,
-                                                      P.cr, P.perm, P.xs[s.cur], P.cs[s.cur]);
+                                                      P.cr, P.perm, P.xs[s.cur], P.cs[s.cur], P.xs0);
     if (nk) *nk += 1;
   }
   return cudaGetLastError();
@@ -1406,6 +1436,7 @@ CoupleArgs couple_args(const State& s) {
   A.xsn = P.xs[n];
   A.csn = P.cs[n];
   A.keep_cells = s.phy.rebin > 1;
+  A.xs0 = P.xs0;
   A.nb_mode = s.phy.rebin > 1 ? s.nb_mode : 0;
   A.move_consts = s.phy.rebin > 1 ? s.move_consts : 1;
   A.nb_max = P.nb_max;

@@ -235,6 +235,8 @@ struct Physics {
   double skin;            // largest displacement allowed away from the cell of the last
                           // rebuild (or the step start when sub-cycling): (1 - d_max) / 2
   int rebin;              // cell-list rebuild period in steps (>= 1)
+  double disp_skin;       // kept cell list: largest displacement per axis from the position at
+                          // the rebuild, (1 - d_max) / 4; bounds the recorded candidates
 };
 
 // Tile of lattice cells handled by one CTA of the particle kernel.
@@ -288,6 +290,7 @@ struct Particles {
   int* ti;        // [np][3][4] cell index per axis and node
   double* tw;     // [np][3][4] weight per axis and node
   // kept cell list (rebin_every > 1): contact candidates recorded at the rebuild
+  float4* xs0;    // [np] in-cell offsets at the last rebuild, by slot
   unsigned* nb;   // [nb_max][np] candidate slots
   int* nbn;       // [np] candidate count, -1 when more than nb_max
   int nb_max;
