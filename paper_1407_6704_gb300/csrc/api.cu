@@ -40,7 +40,7 @@ size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
   size_t f, F, mom, red, err, out, X, U, rad, mass, Ap, buoy, gw, cf, pid, rl, jl, Fs, ti, tw, nb, nbn, xs0, xr, cr, xs, cs, g, Fc, key, rank, perm, bin,
-      bsum;
+      bsum, tflag, tbusy, tfree, tblk, tn;
   size_t total;
 };
 
@@ -184,6 +184,12 @@ Layout layout(const pibm_config* c) {
   L.perm = take(sizeof(unsigned) * np);
   L.bin = take(sizeof(unsigned) * (nbin + 1));
   L.bsum = take(sizeof(unsigned) * scan_blocks);
+  const long long ntiles = nbin / bin_map(c).tc;
+  L.tflag = take(np > 0 ? sizeof(int) * ntiles : 0);
+  L.tbusy = take(np > 0 ? sizeof(int) * ntiles : 0);
+  L.tfree = take(np > 0 ? sizeof(int) * ntiles : 0);
+  L.tblk = take(np > 0 ? sizeof(unsigned) * ((ntiles + TILE_BLOCK - 1) / TILE_BLOCK) : 0);
+  L.tn = take(np > 0 ? sizeof(unsigned) * 2 : 0);
   L.total = off;
   return L;
 }
@@ -425,6 +431,8 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
     for (long long p = 0; p < cfg->n_particles; ++p) dmax = fmax(dmax, cfg->diameter[p]);
     s.phy.skin = 0.5 * (1.0 - dmax);
     s.phy.disp_skin = 0.25 * (1.0 - dmax);
+    s.phy.skinf = (float)s.phy.skin;
+    s.phy.disp_skinf = (float)s.phy.disp_skin;
   }
   s.precision = cfg->precision;
   s.deterministic = cfg->deterministic ? 1 : 0;
@@ -481,6 +489,12 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
   P.bm = bin_map(cfg);
   P.nbin = bin_count(cfg);
   P.scan_blocks = (int)((P.nbin + 1 + 8191) / 8192);
+  P.ntiles = P.nbin / P.bm.tc;
+  P.tflag = (int*)(base + L.tflag);
+  P.tbusy = (int*)(base + L.tbusy);
+  P.tfree = (int*)(base + L.tfree);
+  P.tblk = (unsigned*)(base + L.tblk);
+  P.tn = (unsigned*)(base + L.tn);
   s.cur = 0;
 
   cudaStream_t st = h->stream;
@@ -556,12 +570,12 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
       return fail(PIBM_ECUDA);
   }
   if (cudaStreamSynchronize(st) != cudaSuccess) return fail(PIBM_ECUDA);
-  // binning 5 (+1 ordered bins), contacts 1, moments + coupling 2 (+1 ordered
-  // gather), collide 1; with S DEM sub-steps the contacts and the coupling become
-  // 1 + 2 S (+1 spread unless gathered)
+  // binning 5 (+1 ordered bins) and tile lists 2, contacts 1, moments + coupling
+  // 2 (+1 ordered gather), collide 1; with S DEM sub-steps the contacts and the
+  // coupling become 1 + 2 S (+1 spread unless gathered)
   {
     const int S = s.phy.substeps, det = s.deterministic;
-    h->kernels_per_step = np == 0 ? 1 : (S <= 1 ? (det ? 11 : 9) : (det ? 10 : 9) + 2 * S);
+    h->kernels_per_step = np == 0 ? 1 : (S <= 1 ? (det ? 13 : 11) : (det ? 12 : 11) + 2 * S);
   }
   *out = h;
   return PIBM_OK;

@@ -195,6 +195,116 @@ __global__ void k_bin_sort(const unsigned* __restrict__ key, const unsigned* __r
   }
 }
 
+// Tile lists. A tile is busy when it or one of its 3^d neighbours (wrapped on
+// periodic axes) holds a particle. Until the next rebuild every particle stays
+// within the skin (< 1/2 cell) of its cell, so each cell of its delta stencil
+// (at most two cells to either side) and of its Lagrange block lies in a busy
+// tile; the moment and force fields of the free tiles are never touched.
+// Pass 1: the busy flag of every tile and the number of busy tiles per block.
+template <int D>
+__global__ void __launch_bounds__(TILE_BLOCK) k_tile_flags(const unsigned* __restrict__ start,
+                                                           BinMap bm, Geometry g, long long ntiles,
+                                                           int* __restrict__ flag,
+                                                           unsigned* __restrict__ tblk) {
+  const long long t = blockIdx.x * (long long)TILE_BLOCK + threadIdx.x;
+  int busy = 0;
+  if (t < ntiles) {
+    const int tt[3] = {(int)(t % bm.nt[0]), (int)((t / bm.nt[0]) % bm.nt[1]),
+                       (int)(t / ((long long)bm.nt[0] * bm.nt[1]))};
+#pragma unroll 1
+    for (int o = 0; o < (D == 3 ? 27 : 9); ++o) {
+      const int off[3] = {o % 3 - 1, (o / 3) % 3 - 1, D == 3 ? o / 9 - 1 : 0};
+      int nb[3];
+      bool ok = true;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        nb[a] = tt[a] + off[a];
+        if (nb[a] < 0 || nb[a] >= bm.nt[a]) {
+          if (g.periodic[a]) nb[a] = (nb[a] + bm.nt[a]) % bm.nt[a];
+          else ok = false;
+        }
+      }
+      if (!ok) continue;
+      const unsigned long long n =
+          (unsigned long long)nb[0] + bm.nt[0] * ((unsigned long long)nb[1] + bm.nt[1] * (unsigned long long)nb[2]);
+      if (start[(n + 1) * bm.tc] != start[n * bm.tc]) {
+        busy = 1;
+        break;
+      }
+    }
+    flag[t] = busy;
+  }
+  const int cnt = __syncthreads_count(busy);
+  if (threadIdx.x == 0) tblk[blockIdx.x] = (unsigned)cnt;
+}
+
+// Pass 2: each tile's place in the busy or the free list (block prefix of the
+// pass-1 counts plus the rank inside the block), and the two list lengths.
+__global__ void __launch_bounds__(TILE_BLOCK) k_tile_lists(const int* __restrict__ flag,
+                                                           const unsigned* __restrict__ tblk,
+                                                           long long ntiles, int* __restrict__ tbusy,
+                                                           int* __restrict__ tfree,
+                                                           unsigned* __restrict__ tn) {
+  __shared__ unsigned red[32], wsum[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long t = blockIdx.x * (long long)TILE_BLOCK + threadIdx.x;
+  // busy tiles of the blocks before this one, and of all blocks
+  unsigned before = 0, all = 0;
+  const int nblk = (int)((ntiles + TILE_BLOCK - 1) / TILE_BLOCK);
+  for (int b = threadIdx.x; b < nblk; b += TILE_BLOCK) {
+    const unsigned c = tblk[b];
+    all += c;
+    if (b < (int)blockIdx.x) before += c;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    before += __shfl_xor_sync(0xffffffffu, before, o);
+    all += __shfl_xor_sync(0xffffffffu, all, o);
+  }
+  if (lane == 0) {
+    red[wid] = before;
+    wsum[wid] = all;
+  }
+  const bool busy = t < ntiles && flag[t] != 0;
+  __syncthreads();
+  if (wid == 0) {
+    unsigned a = red[lane], b = wsum[lane];
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+      red[0] = a;
+      wsum[0] = b;
+    }
+  }
+  __syncthreads();
+  const unsigned base = red[0], total = wsum[0];
+  // rank among the busy tiles of this block
+  const unsigned m = __ballot_sync(0xffffffffu, busy);
+  __syncthreads();
+  if (lane == 0) red[wid] = __popc(m);
+  __syncthreads();
+  if (wid == 0) {
+    const unsigned v = red[lane];
+    unsigned incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    red[lane] = incl - v;  // exclusive prefix over warps
+  }
+  __syncthreads();
+  const unsigned rank = base + red[wid] + __popc(m & ((1u << lane) - 1u));
+  if (t < ntiles) {
+    if (busy) tbusy[rank] = (int)t;
+    else tfree[t - rank] = (int)t;
+  }
+  if (t == 0) {
+    tn[0] = total;
+    tn[1] = (unsigned)(ntiles - total);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Delta weights along one axis (Eqs. 10-11 and the 2-point hat)
 // ---------------------------------------------------------------------------
@@ -468,7 +578,7 @@ __global__ void __launch_bounds__(256) k_contacts(CoupleArgs A) {
   auto Xat = [&](int k, unsigned i) { return SUB ? A.Xn[k * np + i] : A.X[k * np + i]; };
   auto Uat = [&](int k, unsigned i) { return SUB ? A.Un[k * np + i] : A.U[k * np + i]; };
   const unsigned me_i = SUB ? (unsigned)sl : p;
-  const float mrg = A.xf_margin + (SUB ? 2.f * (float)A.ph.skin : 0.f);
+  const float mrg = A.xf_margin + (SUB ? 2.f * A.ph.skinf : 0.f);
   const float4 me = A.xs[sl];
   const float xp[3] = {me.x, me.y, me.z};
   const float rpf = me.w;
@@ -541,7 +651,7 @@ __global__ void __launch_bounds__(256) k_contacts(CoupleArgs A) {
       const float s = (float)dc + (xp[k] - oq[k]);
       d2f += s * s;
     }
-    const float reach = rpf + o.w + 2.f * (float)A.ph.disp_skin * sqrtf((float)D) + mrg;
+    const float reach = rpf + o.w + 2.f * A.ph.disp_skinf * sqrtf((float)D) + mrg;
     return d2f <= reach * reach;
   };
   // NB: 0 traverse the cells, 1 traverse and record the candidates, 2 take the
@@ -633,16 +743,17 @@ struct MomentsShape {
   static constexpr int KT = CPT * 256 / TC;
 };
 
-// Post-stream moments of every cell of the tiles that hold particles or touch
-// a tile that does (the 2-cell delta stencil never reaches further), KT tiles of
-// TileDims cells per CTA: mom[0] = sum of stored values (rho - S), mom[1..d] = j.
-// Each thread issues the loads of all its cells before it sums any of them.
-// A cell whose neighbours all lie inside the lattice (no wall, no wrap) reads
-// its sources at fixed 32-bit offsets; only cells on the lattice faces take the
-// general path. Cells of other tiles are left untouched; no stencil reads them.
+// Post-stream moments of every cell of the busy tiles (k_tile_lists), KT tiles
+// of TileDims cells per CTA: mom[0] = sum of stored values (rho - S),
+// mom[1..d] = j. Each thread issues the loads of all its cells before it sums
+// any of them. A cell whose neighbours all lie inside the lattice (no wall, no
+// wrap) reads its sources at fixed 32-bit offsets; only cells on the lattice
+// faces take the general path. Cells of free tiles are left untouched; no
+// stencil reads them.
 template <int Q, class St>
 __global__ void __launch_bounds__(256, MomentsShape<Q, St>::MINB) k_moments(Geometry g, BinMap bm,
-                                                 const unsigned* __restrict__ start,
+                                                 const int* __restrict__ tbusy,
+                                                 const unsigned* __restrict__ tn,
                                                  const typename St::T* __restrict__ f,
                                                  typename St::R* __restrict__ mom) {
   using Sh = MomentsShape<Q, St>;
@@ -650,41 +761,20 @@ __global__ void __launch_bounds__(256, MomentsShape<Q, St>::MINB) k_moments(Geom
   using T = typename St::T;
   using R = typename St::R;
   constexpr int D = Sh::D;
-  constexpr int NB = D == 3 ? 27 : 9;
   using TD = TileDims<D>;
   __shared__ int busy[Sh::KT];
   __shared__ int corner[Sh::KT][3];  // first cell of each tile
-  const int ntiles = bm.nt[0] * bm.nt[1] * bm.nt[2];
-  const int tile0 = blockIdx.x * Sh::KT;
+  const int nbusy = (int)tn[0];
+  const int i0 = blockIdx.x * Sh::KT;
+  if (i0 >= nbusy) return;  // the list is shorter than the grid
   if (threadIdx.x < Sh::KT) {
-    const int tile = tile0 + threadIdx.x;
+    const int i = i0 + threadIdx.x;
+    const int tile = i < nbusy ? tbusy[i] : 0;
     const int r = tile / bm.nt[0];
-    busy[threadIdx.x] = 0;
+    busy[threadIdx.x] = i < nbusy;
     corner[threadIdx.x][0] = (tile - r * bm.nt[0]) * TD::TX;
     corner[threadIdx.x][1] = (r % bm.nt[1]) * TD::TY;
     corner[threadIdx.x][2] = (r / bm.nt[1]) * TD::TZ;
-  }
-  __syncthreads();
-  if (threadIdx.x < Sh::KT * NB) {
-    const int k = threadIdx.x / NB, o = threadIdx.x % NB;
-    if (tile0 + k < ntiles) {
-      const int t[3] = {corner[k][0] / TD::TX, corner[k][1] / TD::TY, corner[k][2] / TD::TZ};
-      const int off[3] = {o % 3 - 1, (o / 3) % 3 - 1, D == 3 ? o / 9 - 1 : 0};
-      int nb[3];
-      bool ok = true;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        nb[a] = t[a] + off[a];
-        if (nb[a] < 0 || nb[a] >= bm.nt[a]) {
-          if (g.periodic[a]) nb[a] = (nb[a] + bm.nt[a]) % bm.nt[a];
-          else ok = false;
-        }
-      }
-      if (ok) {
-        const unsigned nt = (unsigned)(nb[0] + bm.nt[0] * (nb[1] + bm.nt[1] * nb[2]));
-        if (start[(nt + 1) * (unsigned)TD::TC] != start[nt * (unsigned)TD::TC]) busy[k] = 1;
-      }
-    }
   }
   __syncthreads();
   const int n0 = g.n[0], n01 = g.n[0] * g.n[1];
@@ -698,7 +788,7 @@ __global__ void __launch_bounds__(256, MomentsShape<Q, St>::MINB) k_moments(Geom
     const int x = corner[k][0] + i % TD::TX;
     const int y = corner[k][1] + (i / TD::TX) % TD::TY;
     const int z = corner[k][2] + i / (TD::TX * TD::TY);
-    on[c] = tile0 + k < ntiles && busy[k] && x < g.n[0] && y < g.n[1] && z < g.n[2];
+    on[c] = busy[k] && x < g.n[0] && y < g.n[1] && z < g.n[2];
     cell[c] = x + n0 * y + n01 * z;
     if (!on[c]) continue;
     const bool inner = x >= 1 && x <= g.n[0] - 2 && y >= 1 && y <= g.n[1] - 2 &&
@@ -804,7 +894,36 @@ __device__ __forceinline__ void particle_taps(const Geometry& g, const int4& mc,
   }
 }
 
+// a[i] for a loop index the compiler does not unroll, by selects (the array
+// stays in registers instead of local memory).
+template <typename T, int W>
+__device__ __forceinline__ T pick(const T (&a)[W], int i) {
+  T v = a[0];
+#pragma unroll
+  for (int k = 1; k < W; ++k) v = i == k ? a[k] : v;
+  return v;
+}
+
+// Every per-axis tap index inside [0, n) (then every tap cell lies in the
+// lattice). The tap builders wrap or clamp each index, so this holds for any
+// position; it is checked once per particle instead of at every tap.
+template <int D, int WI, typename R>
+__device__ __forceinline__ bool taps_in_lattice(const Geometry& g, const Taps<WI, R>& tx,
+                                                const Taps<WI, R>& ty, const Taps<WI, R>& tz) {
+  bool ok = true;
+#pragma unroll
+  for (int i = 0; i < WI; ++i) {
+    ok &= (unsigned)tx.idx[i] < (unsigned)g.n[0];
+    ok &= (unsigned)ty.idx[i] < (unsigned)g.n[1];
+    if constexpr (D == 3) ok &= (unsigned)tz.idx[i] < (unsigned)g.n[2];
+  }
+  return ok;
+}
+
 // Eq. (4) on the moments: rs = sum w (rho - S), js = sum w j over the taps.
+// The loads of one stencil row are all issued before any of them is summed;
+// a dropped wall node repeats an in-lattice index with weight 0 and is summed
+// like the others (it adds zero).
 template <int D, int WI, typename R>
 __device__ __forceinline__ void gather_moments(const CoupleArgs& A, const Taps<WI, R>& tx,
                                                const Taps<WI, R>& ty, const Taps<WI, R>& tz,
@@ -814,32 +933,33 @@ __device__ __forceinline__ void gather_moments(const CoupleArgs& A, const Taps<W
   const R* mom = (const R*)A.mom;
   rs = R(0);
   js[0] = js[1] = js[2] = R(0);
+  if (!taps_in_lattice<D, WI, R>(g, tx, ty, tz)) {
+    atomicOr(A.err, ERR_INDEX);
+    return;
+  }
 #pragma unroll 1
   for (int iz = 0; iz < WZ; ++iz) {
     R wz = R(1);
     long long zoff = 0;
     if constexpr (D == 3) {
-      wz = tz.w[iz];
-      zoff = (long long)tz.idx[iz] * g.n[1];
+      wz = pick(tz.w, iz);
+      zoff = (long long)pick(tz.idx, iz) * g.n[1];
     }
     if (wz == R(0)) continue;
-#pragma unroll
+    // 2D: the whole stencil unrolled; 3D: one row at a time (registers)
+#pragma unroll(D == 2 ? WI : 1)
     for (int iy = 0; iy < WI; ++iy) {
-      const R wyz = ty.w[iy] * wz;
-      const long long row = (zoff + ty.idx[iy]) * g.n[0];
+      const R wyz = pick(ty.w, iy) * wz;
+      const long long row = (zoff + pick(ty.idx, iy)) * g.n[0];
+      R m[WI][4];
+#pragma unroll
+      for (int ix = 0; ix < WI; ++ix) load_moments<R>(mom, row + tx.idx[ix], m[ix]);
 #pragma unroll
       for (int ix = 0; ix < WI; ++ix) {
         const R wt = tx.w[ix] * wyz;
-        if (wt == R(0)) continue;
-        if (row + tx.idx[ix] < 0 || row + tx.idx[ix] >= g.ncell) {
-          atomicOr(A.err, ERR_INDEX);
-          continue;
-        }
-        R m[4];
-        load_moments<R>(mom, row + tx.idx[ix], m);
-        rs += wt * m[0];
+        rs += wt * m[ix][0];
 #pragma unroll
-        for (int k = 0; k < D; ++k) js[k] += wt * m[k + 1];
+        for (int k = 0; k < D; ++k) js[k] += wt * m[ix][k + 1];
       }
     }
   }
@@ -859,8 +979,8 @@ __device__ __forceinline__ void spread_amp(const CoupleArgs& A, const Taps<W, TW
     FT wz = FT(1);
     long long zoff = 0;
     if constexpr (D == 3) {
-      wz = (FT)tz.w[iz];
-      zoff = (long long)tz.idx[iz] * g.n[1];
+      wz = (FT)pick(tz.w, iz);
+      zoff = (long long)pick(tz.idx, iz) * g.n[1];
     }
     if (wz == FT(0)) continue;
 #pragma unroll
@@ -1005,10 +1125,17 @@ __device__ __forceinline__ void advance_particle(const CoupleArgs& A, long long 
     A.Xn[k * np + sl] = xn;
     A.Un[k * np + sl] = Un[k];
     if (A.keep_cells) {
-      // distance from the cell centre, minimum image on periodic axes
-      const double dc = min_image(xn - ((double)cell[k] + 0.5), g.n[k], g.periodic[k]);
-      far |= !(fabs(dc) <= 0.5 + A.ph.skin);
-      off[k] = (float)(dc + 0.5);
+      if constexpr (sizeof(R) == 8) {
+        // distance from the cell centre, minimum image on periodic axes
+        const double dc = min_image(xn - ((double)cell[k] + 0.5), g.n[k], g.periodic[k]);
+        far |= !(fabs(dc) <= 0.5 + A.ph.skin);
+        off[k] = (float)(dc + 0.5);
+      } else {
+        // the same from the offset to the cell's lower face, tested in FP32 (the
+        // rounding moves the bound by about 1e-7 of a cell)
+        off[k] = (float)min_image(xn - (double)cell[k], g.n[k], g.periodic[k]);
+        far |= !(fabsf(off[k] - 0.5f) <= 0.5f + A.ph.skinf);
+      }
     }
   }
   if (bad) atomicOr(A.err, ERR_PARTICLE_NONFINITE);
@@ -1018,7 +1145,7 @@ __device__ __forceinline__ void advance_particle(const CoupleArgs& A, long long 
     const float4 o0 = A.xs0[sl];
     const float q0[3] = {o0.x, o0.y, o0.z};
 #pragma unroll
-    for (int k = 0; k < D; ++k) far |= !(fabsf(off[k] - q0[k]) <= (float)A.ph.disp_skin);
+    for (int k = 0; k < D; ++k) far |= !(fabsf(off[k] - q0[k]) <= A.ph.disp_skinf);
     if (far) atomicOr(A.err, ERR_SKIN);
     // the cell and slot change only at a rebuild (written then and on the step after)
     if (A.move_consts) A.csn[sl] = make_int4(mc.x, mc.y, mc.z, (int)sl);
@@ -1034,7 +1161,7 @@ __device__ __forceinline__ void advance_particle(const CoupleArgs& A, long long 
 // delta kernel of width W. The new state, g and the particle's constants are
 // written at its slot, which becomes its storage position for the next step.
 template <int Q, int W, class St, typename FT, bool LAG>
-__global__ void __launch_bounds__(256, (Lattice<Q>::D == 2 && sizeof(typename St::R) == 4) ? 5 : 1)
+__global__ void __launch_bounds__(256, sizeof(typename St::R) == 4 ? (Lattice<Q>::D == 2 ? 5 : 3) : 2)
     k_couple(CoupleArgs A) {
   using L = Lattice<Q>;
   using R = typename St::R;
@@ -1060,17 +1187,24 @@ __global__ void __launch_bounds__(256, (Lattice<Q>::D == 2 && sizeof(typename St
     }
   }
   if (act) {
+    // The 2D FP32-storage taps come from the cell record alone; loading the
+    // particle state after the gathers keeps it out of their registers.
+    constexpr bool LATE = D == 2 && sizeof(R) == 4;
     double U[3] = {0.0, 0.0, 0.0}, Fc[3] = {0.0, 0.0, 0.0};
+    auto load_state = [&]() {
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-      X[k] = A.X[k * np + p];
-      U[k] = A.U[k * np + p];
-      Fc[k] = A.Fcout[k * np + sl];
-    }
+      for (int k = 0; k < D; ++k) {
+        X[k] = A.X[k * np + p];
+        U[k] = A.U[k * np + p];
+        Fc[k] = A.Fcout[k * np + sl];
+      }
+    };
+    if constexpr (!LATE) load_state();
     // --- interpolation of rho, j (Eq. 4) ---
     particle_taps<D, WI, LAG, R>(g, mc, mf, X, tx, ty, tz);
     R rs, js[3];
     gather_moments<D, WI, R>(A, tx, ty, tz, rs, js);
+    if constexpr (LATE) load_state();
 
     // --- particle update (Eq. 13) and force density (Eqs. 6-7) ---
     advance_particle<D, St, FT>(A, sl, p, mc, mf, X, U, Fc, rs, js, amp);
@@ -1401,6 +1535,14 @@ cudaError_t launch_bin(const State& s, cudaStream_t st, int* nk) {
                                                       P.cr, P.perm, P.xs[s.cur], P.cs[s.cur], P.xs0);
     if (nk) *nk += 1;
   }
+  // the busy and free tile lists of this cell list
+  const unsigned tb = (unsigned)((P.ntiles + TILE_BLOCK - 1) / TILE_BLOCK);
+  if (s.geo.d == 2)
+    k_tile_flags<2><<<tb, TILE_BLOCK, 0, st>>>(P.bin_cnt, P.bm, s.geo, P.ntiles, P.tflag, P.tblk);
+  else
+    k_tile_flags<3><<<tb, TILE_BLOCK, 0, st>>>(P.bin_cnt, P.bm, s.geo, P.ntiles, P.tflag, P.tblk);
+  k_tile_lists<<<tb, TILE_BLOCK, 0, st>>>(P.tflag, P.tblk, P.ntiles, P.tbusy, P.tfree, P.tn);
+  if (nk) *nk += 2;
   return cudaGetLastError();
 }
 
@@ -1472,7 +1614,7 @@ cudaError_t couple_t(const State& s, cudaStream_t st, int* nk) {
   constexpr int KT = MomentsShape<Q, St>::KT;
   const unsigned pb = blocks_for(P.np, 256);
   k_moments<Q, St><<<(unsigned)((ntiles + KT - 1) / KT), 256, 0, st>>>(
-      s.geo, P.bm, P.bin_cnt, (const T*)s.f[s.cur], (R*)s.mom);
+      s.geo, P.bm, P.tbusy, P.tn, (const T*)s.f[s.cur], (R*)s.mom);
   int n = 1;
   if (s.phy.substeps <= 1) {
     if (s.phy.lagrange) {

@@ -178,14 +178,16 @@ __device__ __forceinline__ void add_force(FT* __restrict__ F, long long c, const
   }
 }
 
+// The moment field is read only after the kernel that writes it has finished,
+// so the loads take the read-only path.
 template <typename R>
 __device__ __forceinline__ void load_moments(const R* __restrict__ mom, long long c, R (&m)[4]) {
   if constexpr (sizeof(R) == 4) {
-    const float4 a = reinterpret_cast<const float4*>(mom)[c];
+    const float4 a = __ldg(reinterpret_cast<const float4*>(mom) + c);
     m[0] = a.x; m[1] = a.y; m[2] = a.z; m[3] = a.w;
   } else {
-    const double2 a = reinterpret_cast<const double2*>(mom)[2 * c];
-    const double2 b = reinterpret_cast<const double2*>(mom)[2 * c + 1];
+    const double2 a = __ldg(reinterpret_cast<const double2*>(mom) + 2 * c);
+    const double2 b = __ldg(reinterpret_cast<const double2*>(mom) + 2 * c + 1);
     m[0] = a.x; m[1] = a.y; m[2] = b.x; m[3] = b.y;
   }
 }
@@ -237,6 +239,7 @@ struct Physics {
   int rebin;              // cell-list rebuild period in steps (>= 1)
   double disp_skin;       // kept cell list: largest displacement per axis from the position at
                           // the rebuild, (1 - d_max) / 4; bounds the recorded candidates
+  float skinf, disp_skinf;  // the same two in FP32 (tests on FP32 offsets)
 };
 
 // Tile of lattice cells handled by one CTA of the particle kernel.
@@ -303,7 +306,19 @@ struct Particles {
   BinMap bm;
   long long nbin;         // tiles * cells per tile (>= ncell)
   int scan_blocks;
+  // tile lists, rebuilt with the cell list: the tiles that hold a particle or
+  // touch one that does (busy: every stencil cell of the period lies in them)
+  // and the others (free), each in tile order
+  long long ntiles;
+  int* tflag;       // [ntiles] busy flag (scratch of the list build)
+  int* tbusy;       // [ntiles]
+  int* tfree;       // [ntiles]
+  unsigned* tblk;   // [tile_blocks] busy tiles per block of TILE_BLOCK tiles
+  unsigned* tn;     // [2] number of busy and free tiles
 };
+
+// Tiles per CTA of the tile-list kernels.
+constexpr int TILE_BLOCK = 1024;
 
 struct State {
   Geometry geo;

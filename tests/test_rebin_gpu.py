@@ -100,13 +100,14 @@ def test_kept_cell_list_fp32():
 
 
 def test_launch_count_follows_the_rebuild_period():
-    """9 kernels on a rebuild step (binning 5, contacts, moments, coupling,
-    collide), 4 on the others; graph replays are counted like single steps."""
+    """11 kernels on a rebuild step (binning 5, tile lists 2, contacts, moments,
+    coupling, collide), 4 on the others; graph replays are counted like single
+    steps."""
     c = _dense(9, (24, 20), 85, 100)
     got, _ = _run(c, 23, rebin=5, chunks=[3, 20])
     rebuilds = len(range(0, 23, 5))
-    assert got["kps"] == 9
-    assert got["launches"] == 9 * rebuilds + 4 * (23 - rebuilds)
+    assert got["kps"] == 11
+    assert got["launches"] == 11 * rebuilds + 4 * (23 - rebuilds)
 
 
 def test_particle_leaving_its_cell_skin_is_reported():

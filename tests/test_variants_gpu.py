@@ -94,7 +94,7 @@ def test_subcycled_dem_parity_fp64(q, n, S, contact):
     c = _dense(q, n, 42, 160 if q == 9 else 120, dia=(0.5, 0.7))
     got, ref = run_variant(c, 40, contact=contact, young=0.3, substeps=S)
     assert np.count_nonzero(np.abs(ref.Fc).sum(1)) >= 10
-    assert got["kernels"] == 9 + 2 * S
+    assert got["kernels"] == 11 + 2 * S
     print("substeps", S, contact, check(got, ref, c["X"]))
 
 
