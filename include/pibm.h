@@ -80,6 +80,11 @@ extern "C" {
                                    nodes floor(X - 1/2) - 1 .. + 2, the block shifted inside
                                    the domain next to a wall; spreading keeps delta_width */
 
+/* scheduling of a step (results are the same either way) */
+#define PIBM_OVERLAP_AUTO 0 /* on for 2D lattices of at least 2^20 cells where supported */
+#define PIBM_OVERLAP_ON 1   /* on wherever supported */
+#define PIBM_OVERLAP_OFF 2  /* one stream, one collision kernel over the whole lattice */
+
 /* normal contact law */
 #define PIBM_DEM_LINEAR 0 /* k_n delta - gamma v_n, gamma = 2 beta sqrt(m_eff k_n) */
 #define PIBM_DEM_HERTZ 1  /* Eq. (15): (4/3) E* sqrt(R*) delta^{3/2} - gamma v_n,
@@ -154,6 +159,14 @@ typedef struct pibm_config {
                           then, on every axis, which is checked on the device every step
                           (PIBM_EUNSTABLE when violated). Results equal those of R = 1 up to
                           the summation order. Needs dem_substeps <= 1. */
+  int overlap;         /* PIBM_OVERLAP_AUTO (0), PIBM_OVERLAP_ON or PIBM_OVERLAP_OFF.
+                          With overlap a step runs the contact search, then the collision
+                          of the free tiles (those no particle stencil reaches until the
+                          next cell-list rebuild), on a second stream of the handle, beside
+                          the moment and coupling kernels; the collision of the other tiles
+                          follows both. Every cell's arithmetic is unchanged. Supported
+                          with 32- or 64-bit storage and without ordered spreading
+                          (deterministic); elsewhere the step runs on one stream. */
 } pibm_config;
 
 typedef struct pibm_t pibm_t; /* opaque handle owning the device state */

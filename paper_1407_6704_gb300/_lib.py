@@ -26,6 +26,7 @@ PIBM_IMPLICIT, PIBM_EXPLICIT = 0, 1
 PIBM_FP64, PIBM_FP32, PIBM_FP16, PIBM_BF16 = 0, 1, 2, 3
 PIBM_INTERP_DELTA, PIBM_INTERP_LAGRANGE4 = 0, 1
 PIBM_DEM_LINEAR, PIBM_DEM_HERTZ = 0, 1
+PIBM_OVERLAP_AUTO, PIBM_OVERLAP_ON, PIBM_OVERLAP_OFF = 0, 1, 2
 
 FIELD_RHO, FIELD_J, FIELD_POP, FIELD_X, FIELD_U = (1 << k for k in range(5))
 NFIELDS = 5
@@ -68,6 +69,7 @@ class PibmConfig(ctypes.Structure):
         ("wall_poisson", ctypes.c_double),
         ("dem_substeps", ctypes.c_int),
         ("rebin_every", ctypes.c_int),
+        ("overlap", ctypes.c_int),
     ]
 
 

@@ -30,6 +30,11 @@ struct pibm_t {
   int64_t launches;        // kernels launched by pibm_step so far
   int64_t graph_kernels;   // kernels in one replay of the step graphs
   int graph_steps;         // steps in one replay of the step graphs
+  // overlap: contacts and the free tiles' collision on a second stream
+  int split;
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_contacts, ev_free;
+  int side_grid;           // CTAs of the free tiles' collision (a share of the GPU)
 };
 
 namespace {
@@ -71,6 +76,7 @@ int validate(const pibm_config* c) {
   if (!c) return PIBM_EINVAL;
   if (c->lattice != PIBM_D2Q9 && c->lattice != PIBM_D3Q15 && c->lattice != PIBM_D3Q19)
     return PIBM_EINVAL;
+  if (c->overlap < PIBM_OVERLAP_AUTO || c->overlap > PIBM_OVERLAP_OFF) return PIBM_EINVAL;
   const int d = dims_of(c->lattice);
   long long ncell = 1;
   for (int k = 0; k < 3; ++k) {
@@ -223,7 +229,7 @@ void record_error(const char* what, cudaError_t e) {
 
 // One step: the cell list (when due), contacts, coupling, collision. nk
 // receives the number of kernels launched.
-int enqueue_step(pibm_t* h, cudaStream_t st, int* nk_out) {
+int enqueue_step(pibm_t* h, cudaStream_t st, int* nk_out, bool split_ok = true) {
   State& s = h->s;
   int nk = 0;
   const bool rebuild = h->since_rebin == 0;
@@ -232,10 +238,27 @@ int enqueue_step(pibm_t* h, cudaStream_t st, int* nk_out) {
   // between rebuilds the storage order holds, so from the second step after a
   // rebuild the other buffer already holds the constants in that order
   s.move_consts = h->since_rebin <= 1;
-  PHASE(launch_contacts(s, st, &nk));
-  PHASE(launch_couple(s, st, &nk));
-  PHASE(launch_collide_stream(s, st));
-  nk += 1;
+  if (h->split && split_ok) {
+    // side stream: contacts, then the collision of the free tiles (no particle
+    // stencil reaches them, so their force is zero and stays untouched); main
+    // stream: moments, the particle kernels after the contacts, then the busy
+    // tiles' collision after the free ones
+    CK(cudaEventRecord(h->ev_fork, st));
+    CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+    PHASE(launch_contacts(s, h->side, &nk));
+    CK(cudaEventRecord(h->ev_contacts, h->side));
+    PHASE(launch_collide_tiles(s, h->side, 1, h->side_grid));
+    CK(cudaEventRecord(h->ev_free, h->side));
+    PHASE(launch_couple(s, st, &nk, h->ev_contacts));
+    CK(cudaStreamWaitEvent(st, h->ev_free, 0));
+    PHASE(launch_collide_tiles(s, st, 0, 0));
+    nk += 2;
+  } else {
+    PHASE(launch_contacts(s, st, &nk));
+    PHASE(launch_couple(s, st, &nk));
+    PHASE(launch_collide_stream(s, st));
+    nk += 1;
+  }
   s.cur ^= 1;
   h->since_rebin = (h->since_rebin + 1) % s.phy.rebin;
   if (rebuild) h->kernels_per_step = nk;
@@ -571,11 +594,29 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
   }
   if (cudaStreamSynchronize(st) != cudaSuccess) return fail(PIBM_ECUDA);
   // binning 5 (+1 ordered bins) and tile lists 2, contacts 1, moments + coupling
-  // 2 (+1 ordered gather), collide 1; with S DEM sub-steps the contacts and the
-  // coupling become 1 + 2 S (+1 spread unless gathered)
+  // 2 (+1 ordered gather), collide 1 (2 with overlap); with S DEM sub-steps the
+  // contacts and the coupling become 1 + 2 S (+1 spread unless gathered)
   {
     const int S = s.phy.substeps, det = s.deterministic;
     h->kernels_per_step = np == 0 ? 1 : (S <= 1 ? (det ? 13 : 11) : (det ? 12 : 11) + 2 * S);
+  }
+  // overlap: a second stream and its events. AUTO takes it for 2D lattices of
+  // 2^20 cells or more; in 3D the tile-shaped collision (16-cell rows) is slower
+  // than the plain kernel by more than the overlap gains.
+  if (np > 0 && !s.deterministic && collide_tiles_supported(s) &&
+      (cfg->overlap == PIBM_OVERLAP_ON ||
+       (cfg->overlap == PIBM_OVERLAP_AUTO && d == 2 && s.geo.ncell >= (1LL << 20)))) {
+    int lo = 0, hi = 0, sms = 0;
+    if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, lo) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_contacts, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_free, cudaEventDisableTiming) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)
+      return fail(PIBM_ECUDA);
+    h->side_grid = 4 * sms;  // a share of the GPU beside the coupling kernels
+    h->split = 1;
+    h->kernels_per_step += 1;
   }
   *out = h;
   return PIBM_OK;
@@ -837,8 +878,8 @@ static int ensemble_capture(pibm_ensemble_t* e) {
       break;
     }
     const int saved = m->s.cur;
-    rc = enqueue_step(m, ln, nullptr);
-    if (rc == PIBM_OK) rc = enqueue_step(m, ln, nullptr);
+    rc = enqueue_step(m, ln, nullptr, false);
+    if (rc == PIBM_OK) rc = enqueue_step(m, ln, nullptr, false);
     m->s.cur = saved;
     cudaEvent_t join = ev();
     if (rc == PIBM_OK && (!join || cudaEventRecord(join, ln) != cudaSuccess ||
@@ -1015,6 +1056,12 @@ void pibm_destroy(pibm_t* h) {
   for (int i = 0; i < 2; ++i)
     if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
   if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->side) {
+    cudaStreamSynchronize(h->side);
+    cudaStreamDestroy(h->side);
+  }
+  for (cudaEvent_t e : {h->ev_fork, h->ev_contacts, h->ev_free})
+    if (e) cudaEventDestroy(e);
   if (h->owns_ws && h->ws) cudaFree(h->ws);
   delete h;
 }

@@ -138,21 +138,17 @@ __device__ __forceinline__ void take_force(FT* __restrict__ F, long long c, R (&
   if (any) clear_force<D, FT>(F, c);
 }
 
-// Pull-stream, collide, store; one thread per cell. FT: type of the force field.
+// Pull-stream, collide and store the lattice cell (x, y, z).
 template <int Q, class St, typename FT>
-__global__ void __launch_bounds__(256) k_collide_stream(const typename St::T* __restrict__ fin,
-                                                        typename St::T* __restrict__ fout,
-                                                        FT* __restrict__ F, Geometry g,
-                                                        typename St::R om,
-                                                        typename St::R cF,
-                                                        unsigned* __restrict__ err) {
+__device__ __forceinline__ void collide_stream_at(const typename St::T* __restrict__ fin,
+                                                  typename St::T* __restrict__ fout,
+                                                  FT* __restrict__ F, const Geometry& g,
+                                                  typename St::R om, typename St::R cF,
+                                                  unsigned* __restrict__ err, int x, int y,
+                                                  int z) {
   using L = Lattice<Q>;
   using R = typename St::R;
   constexpr int D = L::D;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
-  if (x >= g.n[0] || y >= g.n[1]) return;
   const long long c = x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
   const long long P = g.pitch;
 
@@ -169,6 +165,49 @@ __global__ void __launch_bounds__(256) k_collide_stream(const typename St::T* __
   collide_cell<Q, St>(s, Fv, om, cF, err, out);
 #pragma unroll
   for (int a = 0; a < Q; ++a) fout[a * P + c] = St::store(out[a]);
+}
+
+// Pull-stream, collide, store; one thread per cell. FT: type of the force field.
+template <int Q, class St, typename FT>
+__global__ void __launch_bounds__(256) k_collide_stream(const typename St::T* __restrict__ fin,
+                                                        typename St::T* __restrict__ fout,
+                                                        FT* __restrict__ F, Geometry g,
+                                                        typename St::R om,
+                                                        typename St::R cF,
+                                                        unsigned* __restrict__ err) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= g.n[0] || y >= g.n[1]) return;
+  collide_stream_at<Q, St, FT>(fin, fout, F, g, om, cF, err, x, y, z);
+}
+
+// The same over the tiles of one list (the busy or the free tiles of the cell
+// list, tn[which] of them), one thread per cell of a tile (TileDims), each CTA
+// walking the list with a stride of the grid; the next tile's index is loaded
+// before this tile's populations.
+template <int Q, class St, typename FT>
+__global__ void __launch_bounds__(TileDims<Lattice<Q>::D>::TC)
+    k_collide_tiles(const typename St::T* __restrict__ fin, typename St::T* __restrict__ fout,
+                    FT* __restrict__ F, Geometry g, BinMap bm, const int* __restrict__ tiles,
+                    const unsigned* __restrict__ tn, int which, typename St::R om,
+                    typename St::R cF, unsigned* __restrict__ err) {
+  using TD = TileDims<Lattice<Q>::D>;
+  const int n = (int)tn[which];
+  const int lx = threadIdx.x % TD::TX, ly = (threadIdx.x / TD::TX) % TD::TY,
+            lz = threadIdx.x / (TD::TX * TD::TY);
+  int i = blockIdx.x;
+  int t = i < n ? tiles[i] : 0;
+  for (; i < n; i += gridDim.x) {
+    const int next = i + (int)gridDim.x < n ? tiles[i + gridDim.x] : 0;
+    const int r = t / bm.nt[0];
+    const int x = (t - r * bm.nt[0]) * TD::TX + lx;
+    const int y = (r % bm.nt[1]) * TD::TY + ly;
+    const int z = (r / bm.nt[1]) * TD::TZ + lz;
+    if (x < g.n[0] && y < g.n[1] && z < g.n[2])
+      collide_stream_at<Q, St, FT>(fin, fout, F, g, om, cF, err, x, y, z);
+    t = next;
+  }
 }
 
 // The same for 16-bit storage, two neighbouring cells (x0, x0 + 1) per thread
@@ -493,6 +532,33 @@ struct QOf<Lattice<19>> {
 };
 
 }  // namespace
+
+bool collide_tiles_supported(const State& s) { return !collide_uses_pair_kernel(s); }
+
+cudaError_t launch_collide_tiles(const State& s, cudaStream_t st, int which, int grid) {
+  return dispatch(s, [&](auto lat, auto store, auto ft) {
+    constexpr int Q = QOf<decltype(lat)>::Q;
+    using St = decltype(store);
+    using FT = decltype(ft);
+    using T = typename St::T;
+    using R = typename St::R;
+    const Particles& P = s.p;
+    constexpr int TC = TileDims<Lattice<Q>::D>::TC;
+    if (grid <= 0) {  // every CTA the GPU holds at once
+      int dev = 0, sms = 0, per = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_collide_tiles<Q, St, FT>, TC, 0);
+      if (e != cudaSuccess) return e;
+      grid = sms * (per > 0 ? per : 1);
+    }
+    k_collide_tiles<Q, St, FT><<<grid, TC, 0, st>>>(
+        (const T*)s.f[s.cur], (T*)s.f[1 - s.cur], (FT*)s.F, s.geo, P.bm,
+        which == 0 ? P.tbusy : P.tfree, P.tn, which, (R)s.phy.omega, (R)s.phy.cF, s.err);
+    return cudaGetLastError();
+  });
+}
 
 bool collide_uses_pair_kernel(const State& s) {
   return (s.precision == PIBM_FP16 || s.precision == PIBM_BF16) && (s.geo.n[0] & 1) == 0;

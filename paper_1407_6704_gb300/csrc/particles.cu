@@ -1604,7 +1604,7 @@ CoupleArgs couple_args(const State& s) {
 }
 
 template <int Q, int W, class St, typename FT>
-cudaError_t couple_t(const State& s, cudaStream_t st, int* nk) {
+cudaError_t couple_t(const State& s, cudaStream_t st, int* nk, cudaEvent_t before_particles) {
   const Particles& P = s.p;
   constexpr int D = Lattice<Q>::D;
   using T = typename St::T;
@@ -1615,6 +1615,10 @@ cudaError_t couple_t(const State& s, cudaStream_t st, int* nk) {
   const unsigned pb = blocks_for(P.np, 256);
   k_moments<Q, St><<<(unsigned)((ntiles + KT - 1) / KT), 256, 0, st>>>(
       s.geo, P.bm, P.tbusy, P.tn, (const T*)s.f[s.cur], (R*)s.mom);
+  if (before_particles) {
+    const cudaError_t e = cudaStreamWaitEvent(st, before_particles, 0);
+    if (e != cudaSuccess) return e;
+  }
   int n = 1;
   if (s.phy.substeps <= 1) {
     if (s.phy.lagrange) {
@@ -1664,8 +1668,9 @@ cudaError_t couple_t(const State& s, cudaStream_t st, int* nk) {
 }
 
 template <int Q, class St, typename FT>
-cudaError_t couple_w(const State& s, cudaStream_t st, int* nk) {
-  return s.phy.width == 2 ? couple_t<Q, 2, St, FT>(s, st, nk) : couple_t<Q, 4, St, FT>(s, st, nk);
+cudaError_t couple_w(const State& s, cudaStream_t st, int* nk, cudaEvent_t ev) {
+  return s.phy.width == 2 ? couple_t<Q, 2, St, FT>(s, st, nk, ev)
+                          : couple_t<Q, 4, St, FT>(s, st, nk, ev);
 }
 }  // namespace
 
@@ -1694,25 +1699,25 @@ cudaError_t launch_contacts(const State& s, cudaStream_t st, int* nk) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_couple(const State& s, cudaStream_t st, int* nk) {
+cudaError_t launch_couple(const State& s, cudaStream_t st, int* nk, cudaEvent_t ev) {
   if (s.p.np == 0) return cudaSuccess;
   const int q = s.geo.q;
   if (s.precision == PIBM_FP64) {
-    if (q == 9) return couple_w<9, StoreF64, double>(s, st, nk);
-    if (q == 15) return couple_w<15, StoreF64, double>(s, st, nk);
-    if (q == 19) return couple_w<19, StoreF64, double>(s, st, nk);
+    if (q == 9) return couple_w<9, StoreF64, double>(s, st, nk, ev);
+    if (q == 15) return couple_w<15, StoreF64, double>(s, st, nk, ev);
+    if (q == 19) return couple_w<19, StoreF64, double>(s, st, nk, ev);
   } else if (s.precision == PIBM_FP32) {
-    if (q == 9) return couple_w<9, StoreF32, float>(s, st, nk);
-    if (q == 15) return couple_w<15, StoreF32, float>(s, st, nk);
-    if (q == 19) return couple_w<19, StoreF32, float>(s, st, nk);
+    if (q == 9) return couple_w<9, StoreF32, float>(s, st, nk, ev);
+    if (q == 15) return couple_w<15, StoreF32, float>(s, st, nk, ev);
+    if (q == 19) return couple_w<19, StoreF32, float>(s, st, nk, ev);
   } else if (s.precision == PIBM_FP16) {
-    if (q == 9) return couple_w<9, StoreF16, float>(s, st, nk);
-    if (q == 15) return couple_w<15, StoreF16, float>(s, st, nk);
-    if (q == 19) return couple_w<19, StoreF16, float>(s, st, nk);
+    if (q == 9) return couple_w<9, StoreF16, float>(s, st, nk, ev);
+    if (q == 15) return couple_w<15, StoreF16, float>(s, st, nk, ev);
+    if (q == 19) return couple_w<19, StoreF16, float>(s, st, nk, ev);
   } else if (s.precision == PIBM_BF16) {
-    if (q == 9) return couple_w<9, StoreBF16, float>(s, st, nk);
-    if (q == 15) return couple_w<15, StoreBF16, float>(s, st, nk);
-    if (q == 19) return couple_w<19, StoreBF16, float>(s, st, nk);
+    if (q == 9) return couple_w<9, StoreBF16, float>(s, st, nk, ev);
+    if (q == 15) return couple_w<15, StoreBF16, float>(s, st, nk, ev);
+    if (q == 19) return couple_w<19, StoreBF16, float>(s, st, nk, ev);
   }
   return cudaErrorInvalidValue;
 }

@@ -380,6 +380,11 @@ cudaError_t launch_collide_stream(const State& s, cudaStream_t st);
 // True when the collide-stream runs the two-cells-per-thread 16-bit kernel
 // (its block is 32 wide); the autotuner picks only the block height then.
 bool collide_uses_pair_kernel(const State& s);
+// The same collision over the tiles of one list of the cell list (which = 0:
+// busy, 1: free), `grid` CTAs walking the list; the two together cover every
+// cell once. Available for 32- and 64-bit storage.
+bool collide_tiles_supported(const State& s);
+cudaError_t launch_collide_tiles(const State& s, cudaStream_t st, int which, int grid);
 // Write plane a of the stored buffer f[cur] from FP64 values src (already
 // un-streamed by the host), or from the rest value w_a when src is NULL.
 cudaError_t launch_store_plane(const State& s, int a, const double* src, cudaStream_t st);
@@ -391,7 +396,10 @@ cudaError_t launch_read_moment(const State& s, int comp, double* dst, cudaStream
 // particle kernel (interpolate, contacts, update, spread).
 cudaError_t launch_bin(const State& s, cudaStream_t st, int* nkernels);
 cudaError_t launch_contacts(const State& s, cudaStream_t st, int* nkernels);
-cudaError_t launch_couple(const State& s, cudaStream_t st, int* nkernels);
+// When before_particles is given, the stream waits for it after the moment
+// kernel and before the particle kernels (the contacts then run elsewhere).
+cudaError_t launch_couple(const State& s, cudaStream_t st, int* nkernels,
+                          cudaEvent_t before_particles = nullptr);
 cudaError_t launch_particle_forces(const State& s, double* f_fpi, double* f_c, cudaStream_t st);
 // X or U of the current state (SoA by storage position) into aos[user index][d].
 cudaError_t launch_interleave(const State& s, const double* soa, double* aos, cudaStream_t st);

@@ -44,12 +44,14 @@ class Pibm:
                  precision="fp64", deterministic=False, kn=1e-2, restitution=0.9, x0=None,
                  u0=None, diameter=None, density_ratio=None, f0=None, device=None, stream=None,
                  interp="delta", contact="linear", young=1.0, poisson=0.3, wall_young=None,
-                 wall_poisson=None, substeps=1, rebin_every=1):
+                 wall_poisson=None, substeps=1, rebin_every=1, overlap="auto"):
         """interp: "delta" (the spreading kernel) or "lagrange4" (Eq. 5);
         contact: "linear" (kn) or "hertz" (Eq. 15 with young/poisson of the
         particles and of the walls, default the particles'); both use the
         restitution coefficient; substeps: DEM sub-steps per fluid step;
-        rebin_every: cell-list rebuild period in steps (skin-checked)."""
+        rebin_every: cell-list rebuild period in steps (skin-checked);
+        overlap: "auto", "on" or "off", the collision of the particle-free tiles
+        and the contact search on a second stream (same results)."""
         import torch
 
         self._torch = torch
@@ -82,7 +84,9 @@ class Pibm:
             {"linear": _lib.PIBM_DEM_LINEAR, "hertz": _lib.PIBM_DEM_HERTZ}[contact],
             float(young), float(poisson), float(wall_young or 0.0),
             float(poisson if wall_poisson is None else wall_poisson), int(substeps),
-            int(rebin_every))
+            int(rebin_every),
+            {"auto": _lib.PIBM_OVERLAP_AUTO, "on": _lib.PIBM_OVERLAP_ON,
+             "off": _lib.PIBM_OVERLAP_OFF}[overlap])
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
             else torch.device(device)
         nbytes = ctypes.c_size_t()
