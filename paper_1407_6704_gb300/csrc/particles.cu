@@ -1015,18 +1015,32 @@ __device__ __forceinline__ double advance_axis(double x, int n, int periodic, bo
 
 // Ordered spreading: keep the particle's spreading taps at its slot for the
 // gather kernel, which then applies exactly the weights the atomic path would.
+// One axis at a time, with no pointer to the taps: taking their address would
+// move them (and every gather that reads them) to local memory.
+template <int W, typename TW>
+__device__ __forceinline__ void keep_axis(const CoupleArgs& A, long long sl, int k, bool on,
+                                          const Taps<W, TW>& t) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int idx = -1;
+    double w = 0.0;
+#pragma unroll
+    for (int j = 0; j < W; ++j)
+      if (on && j == i) {
+        idx = t.idx[j];
+        w = (double)t.w[j];
+      }
+    A.ti[(sl * 3 + k) * 4 + i] = idx;
+    A.tw[(sl * 3 + k) * 4 + i] = w;
+  }
+}
+
 template <int D, int W, typename TW>
 __device__ __forceinline__ void keep_taps(const CoupleArgs& A, long long sl, const Taps<W, TW>& tx,
                                           const Taps<W, TW>& ty, const Taps<W, TW>& tz) {
-  const Taps<W, TW>* t[3] = {&tx, &ty, &tz};
-#pragma unroll
-  for (int k = 0; k < 3; ++k)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const bool on = k < D && i < W;
-      A.ti[(sl * 3 + k) * 4 + i] = on ? t[k]->idx[i] : -1;
-      A.tw[(sl * 3 + k) * 4 + i] = on ? (double)t[k]->w[i] : 0.0;
-    }
+  keep_axis<W, TW>(A, sl, 0, true, tx);
+  keep_axis<W, TW>(A, sl, 1, true, ty);
+  keep_axis<W, TW>(A, sl, 2, D == 3, tz);
 }
 
 // The particle's constants move with it to its slot.
