@@ -215,8 +215,9 @@ def run_gpu(args, rank, world):
         stream = sim.stream
         sim.step(args.warmup)
         n_launch0 = sim.launch_count
-        # timed region: K steps through pibm_step (two-step CUDA graphs), CUDA
-        # events on the handle's stream, barrier + synchronise on both sides
+        # timed region: K steps through pibm_step (CUDA graphs of one or two cell-list
+        # rebuild periods), CUDA events on the handle's stream, barrier + synchronise
+        # on both sides
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         barrier()
@@ -331,6 +332,8 @@ def run_gpu(args, rank, world):
                    "particles": w.n_particles, "precision": prec,
                    "particle_state": "f64", "parallelism": f"replicas x{world}",
                    "cell_list_rebuild_every": args.rebin,
+                   "overlap": "auto: on for this 2D lattice (contacts and the particle-free "
+                              "tiles' collision on a second stream)",
                    "l2": "inputs larger than L2 (population buffers 2x151 MB f32 / 2x302 MB f64)"},
         "phases_ms_per_step": ph,
         "kernels": kern,
@@ -539,6 +542,22 @@ def run_profile_only(args):
     X, dia, rr = workload_particles(w)
     sim = Pibm.from_workload(w, precision=args.precision, particles=(X, dia, rr),
                              rebin_every=args.rebin)
+    if args.graph:
+        # the timed path: steps through pibm_step (graphs, overlap as configured)
+        sim.step(args.warmup)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(sim.stream)
+        sim.step(args.steps)
+        e1.record(sim.stream)
+        torch.cuda.synchronize()
+        print(json.dumps({"workload": args.workload, "precision": args.precision,
+                          "ms_per_step": e0.elapsed_time(e1) / args.steps,
+                          "kernels_per_rebuild_step": sim.kernels_per_step,
+                          "status": sim.status()}))
+        sim.close()
+        return
     sim.profile_steps(args.warmup)
     ph = sim.profile_steps(args.steps)
     print(json.dumps({"workload": args.workload, "precision": args.precision,
@@ -564,6 +583,8 @@ def main():
                     help="also time the 500-step gradient of the 96^3 FP64 configuration")
     ap.add_argument("--profile-only", action="store_true",
                     help="only run --steps phase-by-phase steps (ncu driver); prints phase times")
+    ap.add_argument("--graph", action="store_true",
+                    help="with --profile-only: run the steps through pibm_step (graphs) instead")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -153,23 +153,42 @@ __device__ __forceinline__ void collide_stream_at(const typename St::T* __restri
   const long long P = g.pitch;
 
   R s[Q];
+  // a cell whose neighbours all lie inside the lattice (no wall, no wrap) pulls
+  // from fixed offsets; only the cells on the lattice faces test every link
+  const bool inner = x >= 1 && x <= g.n[0] - 2 && y >= 1 && y <= g.n[1] - 2 &&
+                     (D == 2 || (z >= 1 && z <= g.n[2] - 2));
+  if (inner) {
+    const int n0 = g.n[0], n01 = g.n[0] * g.n[1];
+    const typename St::T* fa = fin + c;
 #pragma unroll
-  for (int a = 0; a < Q; ++a) {
-    bool bb;
-    long long src = pull_src<Q>(g, x, y, z, a, bb);
-    s[a] = St::load(bb ? fin[opp(a) * P + c] : fin[a * P + src]);
+    for (int a = 0; a < Q; ++a) {
+      s[a] = St::load(fa[-(L::e(a, 0) + n0 * L::e(a, 1) + n01 * L::e(a, 2))]);
+      fa += P;
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+      bool bb;
+      long long src = pull_src<Q>(g, x, y, z, a, bb);
+      s[a] = St::load(bb ? fin[opp(a) * P + c] : fin[a * P + src]);
+    }
   }
   R Fv[3];
   take_force<D, FT, R>(F, c, Fv);
   R out[Q];
   collide_cell<Q, St>(s, Fv, om, cF, err, out);
+  typename St::T* fo = fout + c;
 #pragma unroll
-  for (int a = 0; a < Q; ++a) fout[a * P + c] = St::store(out[a]);
+  for (int a = 0; a < Q; ++a) {
+    *fo = St::store(out[a]);
+    fo += P;
+  }
 }
 
 // Pull-stream, collide, store; one thread per cell. FT: type of the force field.
 template <int Q, class St, typename FT>
-__global__ void __launch_bounds__(256) k_collide_stream(const typename St::T* __restrict__ fin,
+__global__ void __launch_bounds__(256, (Lattice<Q>::D == 3 && sizeof(typename St::T) == 4) ? 5 : 0)
+    k_collide_stream(const typename St::T* __restrict__ fin,
                                                         typename St::T* __restrict__ fout,
                                                         FT* __restrict__ F, Geometry g,
                                                         typename St::R om,
@@ -187,7 +206,8 @@ __global__ void __launch_bounds__(256) k_collide_stream(const typename St::T* __
 // walking the list with a stride of the grid; the next tile's index is loaded
 // before this tile's populations.
 template <int Q, class St, typename FT>
-__global__ void __launch_bounds__(TileDims<Lattice<Q>::D>::TC)
+__global__ void __launch_bounds__(TileDims<Lattice<Q>::D>::TC,
+                                  (Lattice<Q>::D == 2 && sizeof(typename St::T) == 4) ? 7 : 0)
     k_collide_tiles(const typename St::T* __restrict__ fin, typename St::T* __restrict__ fout,
                     FT* __restrict__ F, Geometry g, BinMap bm, const int* __restrict__ tiles,
                     const unsigned* __restrict__ tn, int which, typename St::R om,

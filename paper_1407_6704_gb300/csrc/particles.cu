@@ -245,6 +245,7 @@ __global__ void __launch_bounds__(TILE_BLOCK) k_tile_lists(const int* __restrict
                                                            long long ntiles, int* __restrict__ tbusy,
                                                            int* __restrict__ tfree,
                                                            unsigned* __restrict__ tn) {
+  constexpr int NW = TILE_BLOCK / 32;  // warps
   __shared__ unsigned red[32], wsum[32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const long long t = blockIdx.x * (long long)TILE_BLOCK + threadIdx.x;
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(TILE_BLOCK) k_tile_lists(const int* __restrict
   const bool busy = t < ntiles && flag[t] != 0;
   __syncthreads();
   if (wid == 0) {
-    unsigned a = red[lane], b = wsum[lane];
+    unsigned a = lane < NW ? red[lane] : 0u, b = lane < NW ? wsum[lane] : 0u;
     for (int o = 16; o > 0; o >>= 1) {
       a += __shfl_xor_sync(0xffffffffu, a, o);
       b += __shfl_xor_sync(0xffffffffu, b, o);
@@ -285,7 +286,7 @@ __global__ void __launch_bounds__(TILE_BLOCK) k_tile_lists(const int* __restrict
   if (lane == 0) red[wid] = __popc(m);
   __syncthreads();
   if (wid == 0) {
-    const unsigned v = red[lane];
+    const unsigned v = lane < NW ? red[lane] : 0u;
     unsigned incl = v;
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned u = __shfl_up_sync(0xffffffffu, incl, o);

@@ -318,7 +318,7 @@ struct Particles {
 };
 
 // Tiles per CTA of the tile-list kernels.
-constexpr int TILE_BLOCK = 1024;
+constexpr int TILE_BLOCK = 256;
 
 struct State {
   Geometry geo;

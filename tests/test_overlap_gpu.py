@@ -64,6 +64,10 @@ CASES = [
                                       npart=500, seed=92, dia=(0.4, 0.7), rr=(1.5, 3.0),
                                       band=(0.0, 0.3), u_scale=2e-3, f0_eps=1e-3), 40, 1,
      [3, 37]),
+    # 16 x 20 = 320 tiles: the tile lists span two blocks of their build kernels
+    ("2d_two_list_blocks", dict(q=9, n=(512, 160), periodic=(1, 0), tau=0.7, width=4,
+                                npart=1500, seed=97, dia=(0.5, 0.8), rr=2.0, band=(0.3, 0.7),
+                                u_scale=2e-3, f0_eps=1e-3, e=0.8), 30, 10, [10, 20]),
     ("3d_walls_periodic_x", dict(q=19, n=(40, 24, 36), periodic=(1, 0, 0), tau=0.7, width=4,
                                  npart=400, seed=93, dia=(0.5, 0.8), rr=2.0, band=(0.5, 0.9),
                                  u_scale=2e-3, f0_eps=1e-3, e=0.8), 30, 4, [2, 28]),
