@@ -138,8 +138,11 @@ __device__ __forceinline__ void take_force(FT* __restrict__ F, long long c, R (&
   if (any) clear_force<D, FT>(F, c);
 }
 
-// Pull-stream, collide and store the lattice cell (x, y, z).
-template <int Q, class St, typename FT>
+// Pull-stream, collide and store the lattice cell (x, y, z). HINT (32- and
+// 64-bit storage): 0 plain accesses; 1 loads marked evict-first (the buffer
+// read is dead after this step) and stores evict-last (the next step's moment
+// kernel reads them back); 2 loads evict-first only.
+template <int Q, class St, typename FT, int HINT = 0>
 __device__ __forceinline__ void collide_stream_at(const typename St::T* __restrict__ fin,
                                                   typename St::T* __restrict__ fout,
                                                   FT* __restrict__ F, const Geometry& g,
@@ -152,6 +155,15 @@ __device__ __forceinline__ void collide_stream_at(const typename St::T* __restri
   const long long c = x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
   const long long P = g.pitch;
 
+  using T = typename St::T;
+  static_assert(HINT == 0 || sizeof(T) >= 4, "cache hints are for 32- and 64-bit storage");
+  unsigned long long first = 0, last = 0;
+  if constexpr (HINT != 0) first = l2_policy_evict_first();
+  if constexpr (HINT == 1) last = l2_policy_evict_last();
+  auto ld = [&](const T* a) -> T {
+    if constexpr (HINT != 0) return ld_l2hint(a, first);
+    else return *a;
+  };
   R s[Q];
   // a cell whose neighbours all lie inside the lattice (no wall, no wrap) pulls
   // from fixed offsets; only the cells on the lattice faces test every link
@@ -159,10 +171,10 @@ __device__ __forceinline__ void collide_stream_at(const typename St::T* __restri
                      (D == 2 || (z >= 1 && z <= g.n[2] - 2));
   if (inner) {
     const int n0 = g.n[0], n01 = g.n[0] * g.n[1];
-    const typename St::T* fa = fin + c;
+    const T* fa = fin + c;
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
-      s[a] = St::load(fa[-(L::e(a, 0) + n0 * L::e(a, 1) + n01 * L::e(a, 2))]);
+      s[a] = St::load(ld(fa - (L::e(a, 0) + n0 * L::e(a, 1) + n01 * L::e(a, 2))));
       fa += P;
     }
   } else {
@@ -170,17 +182,18 @@ __device__ __forceinline__ void collide_stream_at(const typename St::T* __restri
     for (int a = 0; a < Q; ++a) {
       bool bb;
       long long src = pull_src<Q>(g, x, y, z, a, bb);
-      s[a] = St::load(bb ? fin[opp(a) * P + c] : fin[a * P + src]);
+      s[a] = St::load(ld(bb ? fin + (opp(a) * P + c) : fin + (a * P + src)));
     }
   }
   R Fv[3];
   take_force<D, FT, R>(F, c, Fv);
   R out[Q];
   collide_cell<Q, St>(s, Fv, om, cF, err, out);
-  typename St::T* fo = fout + c;
+  T* fo = fout + c;
 #pragma unroll
   for (int a = 0; a < Q; ++a) {
-    *fo = St::store(out[a]);
+    if constexpr (HINT == 1) st_l2hint(fo, St::store(out[a]), last);
+    else *fo = St::store(out[a]);
     fo += P;
   }
 }
@@ -205,7 +218,7 @@ __global__ void __launch_bounds__(256, (Lattice<Q>::D == 3 && sizeof(typename St
 // list, tn[which] of them), one thread per cell of a tile (TileDims), each CTA
 // walking the list with a stride of the grid; the next tile's index is loaded
 // before this tile's populations.
-template <int Q, class St, typename FT>
+template <int Q, class St, typename FT, int HINT>
 __global__ void __launch_bounds__(TileDims<Lattice<Q>::D>::TC,
                                   (Lattice<Q>::D == 2 && sizeof(typename St::T) == 4) ? 7 : 0)
     k_collide_tiles(const typename St::T* __restrict__ fin, typename St::T* __restrict__ fout,
@@ -225,7 +238,7 @@ __global__ void __launch_bounds__(TileDims<Lattice<Q>::D>::TC,
     const int y = (r % bm.nt[1]) * TD::TY + ly;
     const int z = (r / bm.nt[1]) * TD::TZ + lz;
     if (x < g.n[0] && y < g.n[1] && z < g.n[2])
-      collide_stream_at<Q, St, FT>(fin, fout, F, g, om, cF, err, x, y, z);
+      collide_stream_at<Q, St, FT, HINT>(fin, fout, F, g, om, cF, err, x, y, z);
     t = next;
   }
 }
@@ -564,18 +577,20 @@ cudaError_t launch_collide_tiles(const State& s, cudaStream_t st, int which, int
     using R = typename St::R;
     const Particles& P = s.p;
     constexpr int TC = TileDims<Lattice<Q>::D>::TC;
+    // busy tiles: their output is read back by the next step's moment kernel
+    constexpr int HB = sizeof(T) >= 4 ? 1 : 0, HF = sizeof(T) >= 4 ? 2 : 0;
+    auto kern = which == 0 ? k_collide_tiles<Q, St, FT, HB> : k_collide_tiles<Q, St, FT, HF>;
     if (grid <= 0) {  // every CTA the GPU holds at once
       int dev = 0, sms = 0, per = 0;
       cudaError_t e = cudaGetDevice(&dev);
       if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_collide_tiles<Q, St, FT>, TC, 0);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, TC, 0);
       if (e != cudaSuccess) return e;
       grid = sms * (per > 0 ? per : 1);
     }
-    k_collide_tiles<Q, St, FT><<<grid, TC, 0, st>>>(
-        (const T*)s.f[s.cur], (T*)s.f[1 - s.cur], (FT*)s.F, s.geo, P.bm,
-        which == 0 ? P.tbusy : P.tfree, P.tn, which, (R)s.phy.omega, (R)s.phy.cF, s.err);
+    kern<<<grid, TC, 0, st>>>((const T*)s.f[s.cur], (T*)s.f[1 - s.cur], (FT*)s.F, s.geo, P.bm,
+                              which == 0 ? P.tbusy : P.tfree, P.tn, which, (R)s.phy.omega,
+                              (R)s.phy.cF, s.err);
     return cudaGetLastError();
   });
 }

@@ -110,6 +110,36 @@ struct StoreBF16 {
   }
 };
 
+// L2 eviction priorities for single accesses (PTX createpolicy and the
+// .L2::cache_hint qualifier): a policy marks the lines an access touches to be
+// evicted first or last.
+__device__ __forceinline__ unsigned long long l2_policy_evict_first() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ unsigned long long l2_policy_evict_last() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ float ld_l2hint(const float* a, unsigned long long pol) {
+  float v;
+  asm("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double ld_l2hint(const double* a, unsigned long long pol) {
+  double v;
+  asm("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_l2hint(float* a, float v, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(pol));
+}
+__device__ __forceinline__ void st_l2hint(double* a, double v, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(a), "d"(v), "l"(pol));
+}
+
 // Force and moment fields are cell-major: FSTRIDE force slots per cell (2 in 2D,
 // 4 in 3D with the last slot unused) and 4 moment slots per cell (rho - S, jx,
 // jy, jz), so that one vector access or one vector atomic moves a whole cell.
