@@ -175,7 +175,7 @@ def test_autograd_function_returns_the_adjoint_gradients():
     L = settling_velocity(tau, rho, x0, **spec)
     (3.0 * L).backward()
     r = settling_gradient(tau=c["tau"], density_ratio=c["density_ratio"], x0=c["x0"], **spec)
-    assert float(L) == r["loss"]
+    assert float(L.detach()) == r["loss"]
     assert float(tau.grad) == 3.0 * r["dtau"]
     assert np.array_equal(rho.grad.numpy(), 3.0 * r["drho"])
     assert np.array_equal(x0.grad.numpy(), 3.0 * r["dx0"])
