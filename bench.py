@@ -128,7 +128,8 @@ class ClockSampler:
 
 
 def collide_bytes_per_cell(q, precision):
-    return 2 * q * (8 if precision == "fp64" else 4)
+    # read and write every population once, in the storage type
+    return 2 * q * {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}[precision]
 
 
 def particle_bytes(d):
@@ -365,6 +366,8 @@ def run_gpu(args, rank, world):
         line["ensemble"] = ensemble_bench(args)
     if args.adjoint:
         line["adjoint"] = adjoint_bench()
+    if args.mixed:
+        line["mixed_precision_3d"] = mixed_precision_bench(args)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, w)
     if dist is not None:
@@ -439,6 +442,47 @@ def every_step_bench(args, w, X, dia, rr):
     sim.close()
     return {"steps": k, "ms_per_step": ms, "value": w.ncell / (ms * 1e-3) / 1e6,
             "unit": "MLUPS", "status": st}
+
+
+def mixed_precision_bench(args, steps=40):
+    """The 3D workload of the mixed-precision storage modes: D3Q19 256^3, walls,
+    tau 0.55, 4M particles (d 0.6, density ratio 2) in the top half, cell list
+    rebuilt every 10 steps, with FP32, FP16 and BF16 population storage
+    (particles FP64 throughout). Per mode: the step time through graphs, the
+    phase-by-phase split, and the collision against its 2 Q s bytes per cell."""
+    import torch
+    from paper_1407_6704_gb300.inputs import preset, workload_particles
+    from paper_1407_6704_gb300.pibm import Pibm
+
+    w = preset("c3")
+    X, dia, rr = workload_particles(w)
+    peak_gbs, peak_src = _peaks()
+    out = {"workload": "D3Q19 256^3 walls, tau 0.55, 4M particles d 0.6 ratio 2 in the top half, "
+                       "4-point delta", "cells": w.ncell, "particles": w.n_particles,
+           "steps": steps, "cell_list_rebuild_every": args.rebin}
+    for prec in ("fp32", "fp16", "bf16"):
+        sim = Pibm.from_workload(w, precision=prec, particles=(X, dia, rr), rebin_every=args.rebin)
+        sim.step(2 * args.rebin)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(sim.stream)
+        sim.step(steps)
+        e1.record(sim.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        k = 10
+        ph = {key: v / k for key, v in sim.profile_steps(k).items()}
+        gbs = w.ncell * collide_bytes_per_cell(w.q, prec) / (ph["collide_stream"] * 1e-3) / 1e9
+        out[prec] = {"ms_per_step": ms, "value": w.ncell / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+                     "phases_ms_per_step": ph,
+                     "collide_bytes_per_cell": collide_bytes_per_cell(w.q, prec),
+                     "collide_gbs": gbs, "collide_frac": gbs / peak_gbs,
+                     "status": sim.status()}
+        sim.close()
+        torch.cuda.empty_cache()
+    out["peak_source"] = f"{peak_src} copy bandwidth"
+    return out
 
 
 def adjoint_bench(steps=500, K=50):
@@ -581,6 +625,8 @@ def main():
     ap.add_argument("--ensemble", type=int, default=1, help="also time the 64-member ensemble")
     ap.add_argument("--adjoint", type=int, default=1,
                     help="also time the 500-step gradient of the 96^3 FP64 configuration")
+    ap.add_argument("--mixed", type=int, default=1,
+                    help="also time the 256^3 3D workload in FP32, FP16 and BF16 storage")
     ap.add_argument("--profile-only", action="store_true",
                     help="only run --steps phase-by-phase steps (ncu driver); prints phase times")
     ap.add_argument("--graph", action="store_true",

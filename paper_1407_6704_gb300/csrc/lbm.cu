@@ -247,8 +247,10 @@ __global__ void __launch_bounds__(TileDims<Lattice<Q>::D>::TC,
 // and one warp per 64 cells of a row: every population row is read with aligned
 // 32-bit pair loads; the value one cell to the left or right comes from the
 // neighbouring lane (warp shuffle), and only the warp's edge lanes and the
-// domain edges load a single extra element. Requires an even n[0].
-template <int Q, class St, typename FT>
+// domain edges load a single extra element. Requires an even n[0]. IX: the
+// index type of offsets inside one population plane (int when the plane pitch
+// fits in 31 bits, which halves the registers of the per-population rows).
+template <int Q, class St, typename FT, typename IX>
 __global__ void __launch_bounds__(256) k_collide_stream_pair(const typename St::T* __restrict__ fin,
                                                              typename St::T* __restrict__ fout,
                                                              FT* __restrict__ F, Geometry g,
@@ -267,15 +269,17 @@ __global__ void __launch_bounds__(256) k_collide_stream_pair(const typename St::
   const int n0 = g.n[0];
   const bool act = x0 < n0;
   const long long P = g.pitch;
-  const long long c0 = x0 + (long long)n0 * (y + (long long)g.n[1] * z);
+  const IX c0 = x0 + (IX)n0 * (y + (IX)g.n[1] * z);
   const unsigned short* fb = reinterpret_cast<const unsigned short*>(fin);
-  auto pair_at = [&](long long idx) -> unsigned {  // idx even
-    return *reinterpret_cast<const unsigned*>(fb + idx);
+  // element i of population plane a
+  auto at = [&](int a, IX i) { return fb + (long long)a * P + i; };
+  auto pair_at = [&](int a, IX i) -> unsigned {  // i even
+    return *reinterpret_cast<const unsigned*>(at(a, i));
   };
 
   // source row of every population: wraps on periodic axes, bounces at walls
   // (then the whole row bounces); three passes keep every load in flight at once
-  long long rowb[Q];
+  IX rowb[Q];
   bool rowbb[Q];
 #pragma unroll
   for (int a = 0; a < Q; ++a) {
@@ -290,30 +294,28 @@ __global__ void __launch_bounds__(256) k_collide_stream_pair(const typename St::
       else bb = true;
     }
     rowbb[a] = bb;
-    rowb[a] = (long long)n0 * (ys + (long long)g.n[1] * zs);
+    rowb[a] = (IX)n0 * (ys + (IX)g.n[1] * zs);
   }
   // pass 1: one aligned pair per population
   unsigned mine[Q];
 #pragma unroll
   for (int a = 0; a < Q; ++a) {
-    const long long pa = (long long)a * P, po = (long long)opp(a) * P;
     mine[a] = 0u;
-    if (act) mine[a] = rowbb[a] ? pair_at(po + c0) : pair_at(pa + rowb[a] + x0);
+    if (act) mine[a] = rowbb[a] ? pair_at(opp(a), c0) : pair_at(a, rowb[a] + x0);
   }
   // pass 2: the single elements the warp's edge lanes and the domain edges need
   unsigned short fix[Q];
 #pragma unroll
   for (int a = 0; a < Q; ++a) {
     const int ex = L::e(a, 0);
-    const long long pa = (long long)a * P, po = (long long)opp(a) * P;
     fix[a] = 0;
     if (ex == 0 || rowbb[a] || !act) continue;
     if (ex > 0 && (lane == 0 || x0 == 0)) {  // needs x0 - 1
-      if (x0 == 0) fix[a] = g.periodic[0] ? fb[pa + rowb[a] + (n0 - 1)] : fb[po + c0];
-      else fix[a] = fb[pa + rowb[a] + x0 - 1];
+      if (x0 == 0) fix[a] = g.periodic[0] ? *at(a, rowb[a] + (n0 - 1)) : *at(opp(a), c0);
+      else fix[a] = *at(a, rowb[a] + x0 - 1);
     } else if (ex < 0 && (lane == 31 || x0 + 2 >= n0)) {  // needs x0 + 2
-      if (x0 + 2 >= n0) fix[a] = g.periodic[0] ? fb[pa + rowb[a]] : fb[po + c0 + 1];
-      else fix[a] = fb[pa + rowb[a] + x0 + 2];
+      if (x0 + 2 >= n0) fix[a] = g.periodic[0] ? *at(a, rowb[a]) : *at(opp(a), c0 + 1);
+      else fix[a] = *at(a, rowb[a] + x0 + 2);
     }
   }
   // pass 3: neighbours through the warp, then the values of the two cells
@@ -512,9 +514,14 @@ cudaError_t collide_stream_t(const State& s, cudaStream_t st) {
     if ((g.n[0] & 1) == 0) {
       dim3 blk = collide_block(s, true);  // blk.x is 32: one warp per 64 cells of a row
       dim3 grd((g.n[0] + 63) / 64, (g.n[1] + blk.y - 1) / blk.y, g.n[2]);
-      k_collide_stream_pair<Q, St, FT><<<grd, blk, 0, st>>>(
-          (const T*)s.f[s.cur], (T*)s.f[1 - s.cur], (FT*)s.F, g, (R)s.phy.omega, (R)s.phy.cF,
-          s.err);
+      if (g.pitch < (1LL << 31))
+        k_collide_stream_pair<Q, St, FT, int><<<grd, blk, 0, st>>>(
+            (const T*)s.f[s.cur], (T*)s.f[1 - s.cur], (FT*)s.F, g, (R)s.phy.omega, (R)s.phy.cF,
+            s.err);
+      else
+        k_collide_stream_pair<Q, St, FT, long long><<<grd, blk, 0, st>>>(
+            (const T*)s.f[s.cur], (T*)s.f[1 - s.cur], (FT*)s.F, g, (R)s.phy.omega, (R)s.phy.cF,
+            s.err);
       return cudaGetLastError();
     }
   }
