@@ -95,10 +95,17 @@ def test_workspace_for_valid_config(lib):
 @pytest.mark.parametrize("field,value", [
     ("tau", 0.5), ("tau", 0.3), ("lattice", 7), ("delta_width", 3), ("coupling", 5),
     ("precision", 9), ("dem_restitution", 0.0), ("dem_restitution", 1.5), ("dem_kn", -1.0),
+    ("overlap", 3), ("overlap", -1),
 ])
 def test_invalid_scalars_rejected(lib, field, value):
     c, keep = _cfg(**{field: value})
     assert _ws(lib, c)[0] == _lib.PIBM_EINVAL
+
+
+def test_overlap_modes_accepted(lib):
+    for mode in (_lib.PIBM_OVERLAP_AUTO, _lib.PIBM_OVERLAP_ON, _lib.PIBM_OVERLAP_OFF):
+        c, keep = _cfg(overlap=mode)
+        assert _ws(lib, c)[0] == 0
 
 
 def test_invalid_particles_rejected(lib):
