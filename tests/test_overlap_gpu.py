@@ -26,7 +26,8 @@ def _built():
     build.build()
 
 
-def _run(c, steps, precision="fp64", rebin=1, chunks=None, overlap="on", oracle=True):
+def _run(c, steps, precision="fp64", rebin=1, chunks=None, overlap="on", oracle=True,
+         deterministic=False):
     from oracle.oracle import Oracle
     from paper_1407_6704_gb300.pibm import Pibm
 
@@ -37,7 +38,8 @@ def _run(c, steps, precision="fp64", rebin=1, chunks=None, overlap="on", oracle=
         ref = Oracle(c["q"], c["n"], c["periodic"], c["tau"], implicit_drag=c["implicit"], **kw)
         ref.step(steps)
     with Pibm(LAT[c["q"]], c["n"], c["periodic"], c["tau"], implicit=c["implicit"],
-              precision=precision, rebin_every=rebin, overlap=overlap, **kw) as sim:
+              precision=precision, rebin_every=rebin, overlap=overlap,
+              deterministic=deterministic, **kw) as sim:
         for k in (chunks or [steps]):
             sim.step(k)
         got = sim.read("pop", "rho", "j", "x", "u")
@@ -86,7 +88,8 @@ def test_overlap_parity_fp64(name, kw, steps, rebin, chunks):
 
 def test_overlap_launches_one_more_kernel_and_needs_32_or_64_bit_storage():
     """The collision becomes two kernels (free tiles, busy tiles) with overlap;
-    16-bit storage keeps one stream and its pair kernel."""
+    16-bit storage keeps one stream and its pair kernel, and so does ordered
+    spreading (its gather writes every cell of the force field)."""
     c = make_case(q=9, n=(64, 48), periodic=(0, 0), tau=0.7, width=4, npart=60, seed=95,
                   band=(0.6, 0.9))
     on, _ = _run(c, 2, overlap="on", oracle=False)
@@ -95,6 +98,9 @@ def test_overlap_launches_one_more_kernel_and_needs_32_or_64_bit_storage():
     h_on, _ = _run(c, 2, precision="fp16", overlap="on", oracle=False)
     h_off, _ = _run(c, 2, precision="fp16", overlap="off", oracle=False)
     assert h_on["kps"] == h_off["kps"] == off["kps"]
+    d_on, _ = _run(c, 2, overlap="on", oracle=False, deterministic=True)
+    d_off, _ = _run(c, 2, overlap="off", oracle=False, deterministic=True)
+    assert d_on["kps"] == d_off["kps"]
 
 
 def test_overlap_fp32_matches_single_stream():
