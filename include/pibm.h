@@ -187,9 +187,13 @@ int pibm_workspace_bytes(const pibm_config* cfg, size_t* bytes);
 int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes, void* stream,
                 pibm_t** out);
 
-/* Advance nsteps coupled time steps, asynchronously on the handle's stream.
- * Health flags raised on the device (non-finite state, escaped particle) are
- * reported by the next synchronising call. */
+/* Advance nsteps coupled time steps, asynchronously on the handle's stream
+ * (whole cell-list rebuild periods are replayed from CUDA graphs). With overlap
+ * the work of each step forks onto a second stream of the handle and joins back
+ * before the step ends, so the handle's stream orders everything after it.
+ * Health flags raised on the device (non-finite state, escaped particle, a
+ * particle beyond the skin of a kept cell list) are reported by the next
+ * synchronising call; after such a flag the state is not meaningful. */
 int pibm_step(pibm_t* h, int64_t nsteps);
 
 /* Per-particle forces of the last step, AoS [n_particles][d] FP64:

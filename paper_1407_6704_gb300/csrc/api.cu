@@ -21,7 +21,7 @@ struct pibm_t {
   size_t ws_bytes;
   int owns_ws;
   int device;
-  cudaGraphExec_t graph[2];  // two-step graphs, indexed by the parity of s.cur
+  cudaGraphExec_t graph[2];  // step graphs (graph_length steps), indexed by the parity of s.cur
   int graph_failed;
   double* out_dev;         // small device scratch for reductions
   int kernels_per_step;
