@@ -195,11 +195,15 @@ __global__ void k_bin_sort(const unsigned* __restrict__ key, const unsigned* __r
   }
 }
 
-// Tile lists. A tile is busy when it or one of its 3^d neighbours (wrapped on
-// periodic axes) holds a particle. Until the next rebuild every particle stays
+// Tile lists. A tile is busy when a particle's cell lies within two cells of it
+// (wrapped on periodic axes). Until the next rebuild every particle stays
 // within the skin (< 1/2 cell) of its cell, so each cell of its delta stencil
 // (at most two cells to either side) and of its Lagrange block lies in a busy
-// tile; the moment and force fields of the free tiles are never touched.
+// tile; the moment and force fields of the free tiles are never touched. Along
+// an axis the cells within two of a tile lie in it and its two neighbours,
+// except on a periodic axis whose last tile is one cell wide: a stencil can
+// then cross that tile and wrap into the next one, so the neighbours two tiles
+// away along that axis count too.
 // Pass 1: the busy flag of every tile and the number of busy tiles per block.
 template <int D>
 __global__ void __launch_bounds__(TILE_BLOCK) k_tile_flags(const unsigned* __restrict__ start,
@@ -211,16 +215,24 @@ __global__ void __launch_bounds__(TILE_BLOCK) k_tile_flags(const unsigned* __res
   if (t < ntiles) {
     const int tt[3] = {(int)(t % bm.nt[0]), (int)((t / bm.nt[0]) % bm.nt[1]),
                        (int)(t / ((long long)bm.nt[0] * bm.nt[1]))};
+    int span[3], w[3];  // neighbour tiles to either side along each axis
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      span[a] = (a < D && g.periodic[a] && g.n[a] % bm.T[a] == 1) ? 2 : 1;
+      w[a] = 2 * span[a] + 1;
+    }
+    const int count = w[0] * w[1] * (D == 3 ? w[2] : 1);
 #pragma unroll 1
-    for (int o = 0; o < (D == 3 ? 27 : 9); ++o) {
-      const int off[3] = {o % 3 - 1, (o / 3) % 3 - 1, D == 3 ? o / 9 - 1 : 0};
+    for (int o = 0; o < count; ++o) {
+      const int off[3] = {o % w[0] - span[0], (o / w[0]) % w[1] - span[1],
+                          D == 3 ? o / (w[0] * w[1]) - span[2] : 0};
       int nb[3];
       bool ok = true;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         nb[a] = tt[a] + off[a];
         if (nb[a] < 0 || nb[a] >= bm.nt[a]) {
-          if (g.periodic[a]) nb[a] = (nb[a] + bm.nt[a]) % bm.nt[a];
+          if (g.periodic[a]) nb[a] = ((nb[a] % bm.nt[a]) + bm.nt[a]) % bm.nt[a];
           else ok = false;
         }
       }

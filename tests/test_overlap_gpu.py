@@ -70,6 +70,12 @@ CASES = [
     ("2d_two_list_blocks", dict(q=9, n=(512, 160), periodic=(1, 0), tau=0.7, width=4,
                                 npart=1500, seed=97, dia=(0.5, 0.8), rr=2.0, band=(0.3, 0.7),
                                 u_scale=2e-3, f0_eps=1e-3, e=0.8), 30, 10, [10, 20]),
+    # periodic y with 33 rows: the last tile row is one cell wide, so stencils of
+    # particles near y = 32 cross it and wrap into row 0, two tiles away
+    ("2d_periodic_one_cell_tile", dict(q=9, n=(64, 33), periodic=(0, 1), tau=0.7, width=4,
+                                       npart=40, seed=98, dia=(0.4, 0.6), rr=2.0,
+                                       band=(0.86, 0.965), u_scale=1e-3, f0_eps=1e-3), 20, 5,
+     [7, 13]),
     ("3d_walls_periodic_x", dict(q=19, n=(40, 24, 36), periodic=(1, 0, 0), tau=0.7, width=4,
                                  npart=400, seed=93, dia=(0.5, 0.8), rr=2.0, band=(0.5, 0.9),
                                  u_scale=2e-3, f0_eps=1e-3, e=0.8), 30, 4, [2, 28]),
