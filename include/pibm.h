@@ -121,7 +121,10 @@ typedef struct pibm_config {
   int coupling;        /* PIBM_IMPLICIT or PIBM_EXPLICIT */
   int precision;       /* PIBM_FP64, PIBM_FP32, PIBM_FP16 or PIBM_BF16 */
   int deterministic;   /* 0: spread with atomics; 1: ordered per-cell gather,
-                          bitwise reproducible run to run */
+                          bitwise reproducible run to run. With particles, a periodic
+                          axis then needs 2 R + 1 cells (and at least 5), R the gather's
+                          reach: 1 for delta_width 2, 2 for 4, plus 1 when rebin_every
+                          > 1; without ordered spreading it needs 5 cells. */
   double dem_kn;       /* contact stiffness */
   double dem_restitution; /* normal restitution coefficient, in (0, 1] */
   int64_t n_particles; /* may be 0 */

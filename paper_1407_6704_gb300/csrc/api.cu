@@ -117,8 +117,12 @@ int validate(const pibm_config* c) {
   if (c->rebin_every > 1 && c->dem_substeps > 1) return PIBM_ENOTSUP;
   if (c->n_particles > 0) {
     if (!c->x0 || !c->diameter || !c->density_ratio) return PIBM_EINVAL;
-    for (int k = 0; k < d; ++k)  // contact and spreading stencils must not alias
-      if (c->boundary[k] == PIBM_PERIODIC && c->n[k] < 5) return PIBM_EINVAL;
+    // contact and spreading stencils must not alias on a periodic axis: the
+    // contact search spans 3 cells, the ordered gather 2 R + 1
+    const int reach = (c->delta_width == 2 ? 1 : 2) + (c->rebin_every > 1 ? 1 : 0);
+    const int nmin = c->deterministic && 2 * reach + 1 > 5 ? 2 * reach + 1 : 5;
+    for (int k = 0; k < d; ++k)
+      if (c->boundary[k] == PIBM_PERIODIC && c->n[k] < nmin) return PIBM_EINVAL;
     for (long long p = 0; p < c->n_particles; ++p) {
       double dia = c->diameter[p], rr = c->density_ratio[p];
       if (!(dia > 0.0 && dia <= 1.0)) return PIBM_EINVAL;

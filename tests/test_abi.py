@@ -139,6 +139,24 @@ def test_periodic_axes_need_five_cells_with_particles(lib):
     assert _ws(lib, c)[0] == 0
 
 
+def test_ordered_gather_needs_its_reach_on_periodic_axes(lib):
+    """The ordered spreading gathers over 2 R + 1 cells per axis (R = 2 for the
+    4-point kernel, plus 1 with a kept cell list); a shorter periodic axis would
+    visit a cell twice."""
+    c, keep = _cfg(deterministic=1, delta_width=4, rebin_every=10)
+    c.boundary[0] = 1
+    c.x0[0] = 2.0
+    for n, ok in ((6, False), (7, True)):
+        c.n[0] = n
+        assert (_ws(lib, c)[0] == 0) == ok, n
+    c.rebin_every = 1
+    c.n[0] = 5
+    assert _ws(lib, c)[0] == 0
+    c.deterministic = 0
+    c.rebin_every = 10
+    assert _ws(lib, c)[0] == 0
+
+
 def test_empty_particle_set_is_valid(lib):
     c, keep = _cfg()
     c.n_particles = 0
