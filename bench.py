@@ -368,6 +368,8 @@ def run_gpu(args, rank, world):
         line["adjoint"] = adjoint_bench()
     if args.mixed:
         line["mixed_precision_3d"] = mixed_precision_bench(args)
+    if args.variants:
+        line["variants"] = variants_bench(args, w, X, dia, rr)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, w)
     if dist is not None:
@@ -444,6 +446,49 @@ def every_step_bench(args, w, X, dia, rr):
             "unit": "MLUPS", "status": st}
 
 
+def _timed_steps(sim, warmup, steps):
+    import torch
+
+    sim.step(warmup)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(sim.stream)
+    sim.step(steps)
+    e1.record(sim.stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def variants_bench(args, w, X, dia, rr, steps=200):
+    """The paper's variants on the headline workload (c2, FP32 storage): the
+    4-point Lagrange interpolant (Eq. 5), the Hertz normal contact (Eq. 15, E = 0.1,
+    nu = 0.3 in lattice units), and Hertz with 4 DEM sub-steps per fluid step (with
+    the every-step cell list that sub-cycling needs). A variant that fails reports
+    its error instead of a time."""
+    import torch
+    from paper_1407_6704_gb300.pibm import Pibm
+
+    specs = {
+        "lagrange4": dict(interp="lagrange4", rebin_every=args.rebin),
+        "hertz": dict(contact="hertz", young=0.1, poisson=0.3, rebin_every=args.rebin),
+        "hertz_substeps4": dict(contact="hertz", young=0.1, poisson=0.3, substeps=4,
+                                rebin_every=1),
+    }
+    out = {"workload": WORKLOAD_DESC, "precision": "fp32", "steps": steps}
+    for name, kw in specs.items():
+        try:
+            sim = Pibm.from_workload(w, precision="fp32", particles=(X, dia, rr), **kw)
+            ms = _timed_steps(sim, 2 * max(kw["rebin_every"], 2), steps)
+            out[name] = {"ms_per_step": ms, "value": w.ncell / (ms * 1e-3) / 1e6,
+                         "unit": "MLUPS", "status": sim.status()}
+            sim.close()
+        except Exception as e:  # reported, not fatal to the benchmark line
+            out[name] = {"error": str(e)[:200]}
+        torch.cuda.empty_cache()
+    return out
+
+
 def mixed_precision_bench(args, steps=40):
     """The 3D workload of the mixed-precision storage modes: D3Q19 256^3, walls,
     tau 0.55, 4M particles (d 0.6, density ratio 2) in the top half, cell list
@@ -481,6 +526,18 @@ def mixed_precision_bench(args, steps=40):
                      "status": sim.status()}
         sim.close()
         torch.cuda.empty_cache()
+    # the paper's own 3D velocity set on the same workload, FP32 storage
+    try:
+        sim = Pibm("d3q15", w.n, w.periodic, w.tau, gravity=w.gravity, delta_width=w.delta_width,
+                   precision="fp32", kn=w.kn, restitution=w.restitution, x0=X, diameter=dia,
+                   density_ratio=rr, rebin_every=args.rebin)
+        ms = _timed_steps(sim, 2 * args.rebin, steps)
+        out["d3q15_fp32"] = {"ms_per_step": ms, "value": w.ncell / (ms * 1e-3) / 1e6,
+                             "unit": "MLUPS", "status": sim.status()}
+        sim.close()
+    except Exception as e:  # reported, not fatal to the benchmark line
+        out["d3q15_fp32"] = {"error": str(e)[:200]}
+    torch.cuda.empty_cache()
     out["peak_source"] = f"{peak_src} copy bandwidth"
     return out
 
@@ -627,6 +684,8 @@ def main():
                     help="also time the 500-step gradient of the 96^3 FP64 configuration")
     ap.add_argument("--mixed", type=int, default=1,
                     help="also time the 256^3 3D workload in FP32, FP16 and BF16 storage")
+    ap.add_argument("--variants", type=int, default=1,
+                    help="also time the Lagrange, Hertz and sub-cycled variants on the workload")
     ap.add_argument("--profile-only", action="store_true",
                     help="only run --steps phase-by-phase steps (ncu driver); prints phase times")
     ap.add_argument("--graph", action="store_true",
