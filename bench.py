@@ -172,6 +172,28 @@ def collide_flops_per_cell_fp64(q):
     return {9: 91, 15: 150, 19: 185}[q]
 
 
+def max_over_ranks(v, dist, device="cuda"):
+    """This rank's v -> the maximum over all ranks (v itself in a single process)."""
+    if dist is None:
+        return v
+    import torch
+
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world, units, ms):
+    """Whole-job throughput: the units every rank processed in one step over the
+    slowest rank's time per step (ms)."""
+    return world * units / (ms * 1e-3)
+
+
+def replica_seed(seed, rank):
+    """Each rank sediments its own independent instance (replicas, no exchange)."""
+    return seed + 1000 * rank
+
+
 def run_gpu(args, rank, world):
     import torch
     from paper_1407_6704_gb300 import build
@@ -186,8 +208,7 @@ def run_gpu(args, rank, world):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w = preset(args.workload)
-    # replicas: each rank sedimentes its own independent instance
-    w.seed = w.seed + 1000 * rank
+    w.seed = replica_seed(w.seed, rank)
     X, dia, rr = workload_particles(w)
     n_stencil = stencil_cells(X, w.n, w.delta_width)
     peak_gbs, peak_src = _peaks()
@@ -201,12 +222,8 @@ def run_gpu(args, rank, world):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def rank_max(v):
+        return max_over_ranks(v, dist)
 
     results = {}
     clocks = None
@@ -232,7 +249,7 @@ def run_gpu(args, rank, world):
         if sampler:
             sampler.__exit__(None, None, None)
             clocks = sampler.summary()
-        ms_graph = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+        ms_graph = rank_max(e0.elapsed_time(e1) / args.steps)
         launches = sim.launch_count - n_launch0
         # second region: the same steps launched phase by phase with CUDA events
         # between the phases (per-kernel durations for the roofline)
@@ -242,7 +259,7 @@ def run_gpu(args, rank, world):
         st = sim.status()
         kps = sim.kernels_per_step
         sim.close()
-        results[prec] = dict(ms=ms_graph, ms_phased=max_over_ranks(ph["total"] / args.steps),
+        results[prec] = dict(ms=ms_graph, ms_phased=rank_max(ph["total"] / args.steps),
                              phases={k: v / args.steps for k, v in ph.items()}, status=st,
                              kps=kps, launches=launches)
         if not args.both:
@@ -259,7 +276,7 @@ def run_gpu(args, rank, world):
     out = sim.read("x", "u")
     sim.close()
     torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_s = rank_max(time.perf_counter() - t0)
     h2d = X.nbytes + dia.nbytes + rr.nbytes
     d2h = out["x"].nbytes + out["u"].nbytes
 
@@ -270,8 +287,8 @@ def run_gpu(args, rank, world):
 
     r = results[prec]
     cells = w.ncell
-    mlups = world * cells / (r["ms"] * 1e-3) / 1e6
-    pups = world * w.n_particles / (r["ms"] * 1e-3)
+    mlups = aggregate_rate(world, cells, r["ms"]) / 1e6
+    pups = aggregate_rate(world, w.n_particles, r["ms"])
     # dominant kernel roofline
     ph = r["phases"]
     algo_cell = collide_bytes_per_cell(w.q, prec)
@@ -360,17 +377,20 @@ def run_gpu(args, rank, world):
             line[p]["collide_roofline"] = {"bound": "alu", "achieved": a,
                                            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                                            "frac": a / FP64_PEAK_TFLOPS}
-    if args.rebin > 1:
+    # the secondary measurements and the CPU baseline belong to the single-GPU run;
+    # a multi-rank (scaling) run reports its replicas' throughput only
+    solo = world == 1
+    if solo and args.rebin > 1:
         line["every_step_rebuild"] = every_step_bench(args, w, X, dia, rr)
-    if args.ensemble:
+    if solo and args.ensemble:
         line["ensemble"] = ensemble_bench(args)
-    if args.adjoint:
+    if solo and args.adjoint:
         line["adjoint"] = adjoint_bench()
-    if args.mixed:
+    if solo and args.mixed:
         line["mixed_precision_3d"] = mixed_precision_bench(args)
-    if args.variants:
+    if solo and args.variants:
         line["variants"] = variants_bench(args, w, X, dia, rr)
-    if not args.no_cpu_baseline:
+    if solo and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, w)
     if dist is not None:
         dist.destroy_process_group()
