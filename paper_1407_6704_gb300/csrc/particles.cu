@@ -1,10 +1,12 @@
 // Particle kernels: the cell list (counting sort of particles into lattice-cell
-// bins) and the coupled particle kernel, which for each particle
+// bins) with its busy and free tile lists, the moment kernel over the busy
+// tiles, the contact kernel, which sums the linear spring-dashpot (or Hertz)
+// contact forces over the 3^d neighbouring bins (or the candidates recorded at
+// the last rebuild) and the walls, and the coupled particle kernel, which for
+// each particle
 //   - interpolates the post-stream moments rho, j of the fluid with the per-axis
 //     delta weights (Eq. 4 of the paper, the interpolant being the same kernel
-//     as the spreading, Eqs. 10-11),
-//   - sums the linear spring-dashpot contact forces over the 3^d neighbouring
-//     bins and the walls,
+//     as the spreading, Eqs. 10-11) or the Lagrange polynomials (Eq. 5),
 //   - advances U and X (Eq. 13, with the drag implicit or explicit),
 //   - forms the force density g = 2 (rho_l U - j_l) of the moving bounce-back
 //     (Eqs. 6-7) and spreads A_p g back to the lattice (Eq. 9).
