@@ -219,7 +219,8 @@ int pibm_invariants(pibm_t* h, double* out);
 int pibm_status(pibm_t* h);
 
 /* Number of kernels one pibm_step(h, 1) launches (for launch accounting); with
- * rebin_every > 1, the count of a step that rebuilds the cell list. */
+ * rebin_every > 1, the count of a step that rebuilds the cell list. With
+ * overlap the collision counts as two kernels (free and busy tiles). */
 int pibm_kernels_per_step(pibm_t* h);
 
 /* Total number of kernels pibm_step has launched on this handle since it was
