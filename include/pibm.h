@@ -309,8 +309,11 @@ const char* pibm_strerror(int status);
  * The first call on each device looks up the array's device address with that
  *   device current (cudaGetSymbolAddress); make that first call before any
  *   stream capture that will contain later calls.
- * Errors: PIBM_EINVAL (NULL pointer, bad lattice or extents), PIBM_ETOOBIG,
- *   PIBM_ECUDA. */
+ * Errors: PIBM_EINVAL (NULL pointer, bad lattice or extents), PIBM_ETOOBIG (any
+ *   extents whose product exceeds the limit, checked without overflow),
+ *   PIBM_ECUDA (the failed call is named by pibm_last_error). On entry the call
+ *   clears any CUDA error still pending on this thread from an earlier call, so
+ *   that it is not reported as this call's own. */
 int pibm_fluid_sums_noalloc(const double* f, int lattice, const int64_t n[3], double* out,
                             void* stream);
 

@@ -44,7 +44,7 @@ constexpr size_t ALIGN = 256;
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-  size_t f, F, mom, red, err, out, X, U, rad, mass, Ap, buoy, gw, cf, pid, rl, jl, Fs, ti, tw, nb, nbn, xs0, xr, cr, xs, cs, g, Fc, key, rank, perm, bin,
+  size_t f, F, mom, red, err, out, X, U, rad, mass, Ap, buoy, gw, cf, pid, rl, jl, Fs, ti, tw, nb, nbn, xs0, xr, cr, xs, cs, g, Fc, Fcf, key, rank, perm, bin,
       bsum, tflag, tbusy, tfree, tblk, tn;
   size_t total;
 };
@@ -189,6 +189,7 @@ Layout layout(const pibm_config* c) {
   L.cs = take(2 * align_up(sizeof(int4) * np));
   L.g = take(sizeof(double) * d * np);
   L.Fc = take(sizeof(double) * d * np);
+  L.Fcf = take(sizeof(float) * d * np);
   L.key = take(sizeof(unsigned) * np);
   L.rank = take(sizeof(unsigned) * np);
   L.perm = take(sizeof(unsigned) * np);
@@ -208,10 +209,7 @@ Layout layout(const pibm_config* c) {
 // Description of the last failed CUDA call on this thread (pibm_last_error).
 thread_local char g_last_error[256] = "";
 
-void record_error(const char* what, cudaError_t e) {
-  snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", what, cudaGetErrorName(e),
-           cudaGetErrorString(e));
-}
+void record_error(const char* what, cudaError_t e) { pibm::record_cuda_error(what, e); }
 
 #define CK(expr)                          \
   do {                                    \
@@ -346,6 +344,11 @@ struct DeviceGuard {
 
 namespace pibm {
 HandleView handle_view(pibm_t* h) { return HandleView{&h->s, h->ws, h->ws_bytes, h->stream}; }
+
+void record_cuda_error(const char* what, cudaError_t e) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", what, cudaGetErrorName(e),
+           cudaGetErrorString(e));
+}
 }  // namespace pibm
 
 extern "C" {
@@ -508,6 +511,7 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
   P.xs0 = cfg->rebin_every > 1 ? (float4*)(base + L.xs0) : nullptr;
   P.nb_max = d == 2 ? 24 : 64;
   P.Fc = (double*)(base + L.Fc);
+  P.Fcf = (float*)(base + L.Fcf);
   P.key = (unsigned*)(base + L.key);
   P.rank = (unsigned*)(base + L.rank);
   P.perm = (unsigned*)(base + L.perm);

@@ -138,33 +138,26 @@ __device__ __forceinline__ void take_force(FT* __restrict__ F, long long c, R (&
   if (any) clear_force<D, FT>(F, c);
 }
 
-// Pull-stream, collide and store the lattice cell (x, y, z). HINT (32- and
-// 64-bit storage): 0 plain accesses; 1 loads marked evict-first (the buffer
-// read is dead after this step) and stores evict-last (the next step's moment
-// kernel reads them back); 2 loads evict-first only.
-template <int Q, class St, typename FT, int HINT = 0>
-__device__ __forceinline__ void collide_stream_at(const typename St::T* __restrict__ fin,
-                                                  typename St::T* __restrict__ fout,
-                                                  FT* __restrict__ F, const Geometry& g,
-                                                  typename St::R om, typename St::R cF,
-                                                  unsigned* __restrict__ err, int x, int y,
-                                                  int z) {
+// The post-stream populations of lattice cell (x, y, z) as stored values s (type
+// R): f*_a(x - e_a), or f*_opp(a)(x) where the link crosses a wall. HINT != 0
+// (32- and 64-bit storage): the loads are marked evict-first (the buffer read
+// is dead after this step).
+template <int Q, class St, int HINT = 0>
+__device__ __forceinline__ void pull_cell(const typename St::T* __restrict__ fin,
+                                          const Geometry& g, int x, int y, int z,
+                                          typename St::R (&s)[Q]) {
   using L = Lattice<Q>;
-  using R = typename St::R;
+  using T = typename St::T;
   constexpr int D = L::D;
+  static_assert(HINT == 0 || sizeof(T) >= 4, "cache hints are for 32- and 64-bit storage");
   const long long c = x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
   const long long P = g.pitch;
-
-  using T = typename St::T;
-  static_assert(HINT == 0 || sizeof(T) >= 4, "cache hints are for 32- and 64-bit storage");
-  unsigned long long first = 0, last = 0;
+  unsigned long long first = 0;
   if constexpr (HINT != 0) first = l2_policy_evict_first();
-  if constexpr (HINT == 1) last = l2_policy_evict_last();
   auto ld = [&](const T* a) -> T {
     if constexpr (HINT != 0) return ld_l2hint(a, first);
     else return *a;
   };
-  R s[Q];
   // a cell whose neighbours all lie inside the lattice (no wall, no wrap) pulls
   // from fixed offsets; only the cells on the lattice faces test every link
   const bool inner = x >= 1 && x <= g.n[0] - 2 && y >= 1 && y <= g.n[1] - 2 &&
@@ -185,8 +178,21 @@ __device__ __forceinline__ void collide_stream_at(const typename St::T* __restri
       s[a] = St::load(ld(bb ? fin + (opp(a) * P + c) : fin + (a * P + src)));
     }
   }
-  R Fv[3];
-  take_force<D, FT, R>(F, c, Fv);
+}
+
+// Collide the pulled values s of cell c with the force Fv of this step and store
+// the post-collision values. HINT == 1: the stores are marked evict-last (the
+// next step's moment kernel reads them back).
+template <int Q, class St, int HINT = 0>
+__device__ __forceinline__ void collide_store(typename St::T* __restrict__ fout,
+                                              const Geometry& g, long long c,
+                                              const typename St::R (&s)[Q],
+                                              const typename St::R (&Fv)[3], typename St::R om,
+                                              typename St::R cF, unsigned* __restrict__ err) {
+  using R = typename St::R;
+  using T = typename St::T;
+  unsigned long long last = 0;
+  if constexpr (HINT == 1) last = l2_policy_evict_last();
   R out[Q];
   collide_cell<Q, St>(s, Fv, om, cF, err, out);
   T* fo = fout + c;
@@ -194,8 +200,30 @@ __device__ __forceinline__ void collide_stream_at(const typename St::T* __restri
   for (int a = 0; a < Q; ++a) {
     if constexpr (HINT == 1) st_l2hint(fo, St::store(out[a]), last);
     else *fo = St::store(out[a]);
-    fo += P;
+    fo += g.pitch;
   }
+}
+
+// Pull-stream, collide and store the lattice cell (x, y, z). HINT (32- and
+// 64-bit storage): 0 plain accesses; 1 loads marked evict-first (the buffer
+// read is dead after this step) and stores evict-last (the next step's moment
+// kernel reads them back); 2 loads evict-first only. NOF: the cell has no
+// force (no particle stencil reaches it, and the force field is not kept).
+template <int Q, class St, typename FT, int HINT = 0, bool NOF = false>
+__device__ __forceinline__ void collide_stream_at(const typename St::T* __restrict__ fin,
+                                                  typename St::T* __restrict__ fout,
+                                                  FT* __restrict__ F, const Geometry& g,
+                                                  typename St::R om, typename St::R cF,
+                                                  unsigned* __restrict__ err, int x, int y,
+                                                  int z) {
+  using R = typename St::R;
+  constexpr int D = Lattice<Q>::D;
+  const long long c = x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
+  R s[Q];
+  pull_cell<Q, St, HINT>(fin, g, x, y, z, s);
+  R Fv[3] = {R(0), R(0), R(0)};
+  if constexpr (!NOF) take_force<D, FT, R>(F, c, Fv);
+  collide_store<Q, St, HINT == 1 ? 1 : 0>(fout, g, c, s, Fv, om, cF, err);
 }
 
 // Pull-stream, collide, store; one thread per cell. FT: type of the force field.
@@ -218,7 +246,7 @@ __global__ void __launch_bounds__(256, (Lattice<Q>::D == 3 && sizeof(typename St
 // list, tn[which] of them), one thread per cell of a tile (TileDims), each CTA
 // walking the list with a stride of the grid; the next tile's index is loaded
 // before this tile's populations.
-template <int Q, class St, typename FT, int HINT>
+template <int Q, class St, typename FT, int HINT, bool NOF = false>
 __global__ void __launch_bounds__(TileDims<Lattice<Q>::D>::TC,
                                   (Lattice<Q>::D == 2 && sizeof(typename St::T) == 4) ? 7 : 0)
     k_collide_tiles(const typename St::T* __restrict__ fin, typename St::T* __restrict__ fout,
@@ -238,7 +266,7 @@ __global__ void __launch_bounds__(TileDims<Lattice<Q>::D>::TC,
     const int y = (r % bm.nt[1]) * TD::TY + ly;
     const int z = (r / bm.nt[1]) * TD::TZ + lz;
     if (x < g.n[0] && y < g.n[1] && z < g.n[2])
-      collide_stream_at<Q, St, FT, HINT>(fin, fout, F, g, om, cF, err, x, y, z);
+      collide_stream_at<Q, St, FT, HINT, NOF>(fin, fout, F, g, om, cF, err, x, y, z);
     t = next;
   }
 }
@@ -571,6 +599,19 @@ struct QOf<Lattice<19>> {
   static constexpr int Q = 19;
 };
 
+// CTAs of a grid-stride kernel that fill the GPU once (grid <= 0), else grid.
+template <class K>
+cudaError_t full_grid(K kern, int threads, int& grid) {
+  if (grid > 0) return cudaSuccess;
+  int dev = 0, sms = 0, per = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, 0);
+  if (e != cudaSuccess) return e;
+  grid = sms * (per > 0 ? per : 1);
+  return cudaSuccess;
+}
+
 }  // namespace
 
 bool collide_tiles_supported(const State& s) { return !collide_uses_pair_kernel(s); }
@@ -586,15 +627,10 @@ cudaError_t launch_collide_tiles(const State& s, cudaStream_t st, int which, int
     constexpr int TC = TileDims<Lattice<Q>::D>::TC;
     // busy tiles: their output is read back by the next step's moment kernel
     constexpr int HB = sizeof(T) >= 4 ? 1 : 0, HF = sizeof(T) >= 4 ? 2 : 0;
-    auto kern = which == 0 ? k_collide_tiles<Q, St, FT, HB> : k_collide_tiles<Q, St, FT, HF>;
-    if (grid <= 0) {  // every CTA the GPU holds at once
-      int dev = 0, sms = 0, per = 0;
-      cudaError_t e = cudaGetDevice(&dev);
-      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, TC, 0);
-      if (e != cudaSuccess) return e;
-      grid = sms * (per > 0 ? per : 1);
-    }
+    cudaError_t e;
+    // the free tiles have no force: no particle stencil reaches them
+    auto kern = which == 0 ? k_collide_tiles<Q, St, FT, HB> : k_collide_tiles<Q, St, FT, HF, true>;
+    if ((e = full_grid(kern, TC, grid)) != cudaSuccess) return e;
     kern<<<grid, TC, 0, st>>>((const T*)s.f[s.cur], (T*)s.f[1 - s.cur], (FT*)s.F, s.geo, P.bm,
                               which == 0 ? P.tbusy : P.tfree, P.tn, which, (R)s.phy.omega,
                               (R)s.phy.cF, s.err);

@@ -97,15 +97,18 @@ double* g_na_ptr[NA_MAX_DEVICES] = {};
 // device with that device current and cached.
 int scratch_for_current_device(double** out) {
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) {
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) {
+    pibm::record_cuda_error("cudaGetDevice", e != cudaSuccess ? e : cudaErrorInvalidDevice);
     cudaGetLastError();
     return PIBM_ECUDA;
   }
   std::lock_guard<std::mutex> lock(g_na_mu);
   if (!g_na_ptr[dev]) {
     void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, na_scratch);
+    e = cudaGetSymbolAddress(&p, na_scratch);
     if (e != cudaSuccess || !p) {
+      pibm::record_cuda_error("cudaGetSymbolAddress", e != cudaSuccess ? e : cudaErrorInvalidSymbol);
       cudaGetLastError();
       return PIBM_ECUDA;
     }
@@ -124,10 +127,14 @@ extern "C" int pibm_fluid_sums_noalloc(const double* f, int lattice, const int64
   if (n[0] < 1 || n[1] < 1 || n[2] < 1) return PIBM_EINVAL;
   if (lattice == PIBM_D2Q9 && n[2] != 1) return PIBM_EINVAL;
   long long ncell = 1;
-  for (int k = 0; k < 3; ++k) {  // stepwise, so the product cannot overflow
+  for (int k = 0; k < 3; ++k) {
+    // checked before multiplying, so the product never overflows
+    if (n[k] > NA_MAX_CELLS / ncell) return PIBM_ETOOBIG;  // beyond the static scratch
     ncell *= n[k];
-    if (ncell > NA_MAX_CELLS) return PIBM_ETOOBIG;  // beyond the static scratch
   }
+  // an error left pending by an earlier, unrelated call on this thread is
+  // cleared here, so that it is not reported as this call's launch failure
+  cudaGetLastError();
   double* part = nullptr;
   int rc = scratch_for_current_device(&part);
   if (rc != PIBM_OK) return rc;
@@ -147,5 +154,10 @@ extern "C" int pibm_fluid_sums_noalloc(const double* f, int lattice, const int64
       k_na_final<4><<<1, NA_THREADS, 0, st>>>(part, nb, out);
       break;
   }
-  return cudaGetLastError() == cudaSuccess ? PIBM_OK : PIBM_ECUDA;
+  const cudaError_t le = cudaGetLastError();
+  if (le != cudaSuccess) {
+    pibm::record_cuda_error("pibm_fluid_sums_noalloc launch", le);
+    return PIBM_ECUDA;
+  }
+  return PIBM_OK;
 }

@@ -323,16 +323,6 @@ __global__ void __launch_bounds__(TILE_BLOCK) k_tile_lists(const int* __restrict
 // ---------------------------------------------------------------------------
 // Delta weights along one axis (Eqs. 10-11 and the 2-point hat)
 // ---------------------------------------------------------------------------
-template <int W, typename WT>
-struct Taps {
-  int first;    // unwrapped index of the first node
-  int idx[W];   // wrapped (periodic) or clamped (dropped wall node) index
-  WT w[W];
-};
-
-__device__ __forceinline__ void sincospi_t(double a, double* s, double* c) { sincospi(a, s, c); }
-__device__ __forceinline__ void sincospi_t(float a, float* s, float* c) { sincospif(a, s, c); }
-
 // b = floor(X - 1/2); nodes b..b+1 (W = 2) or b-1..b+2 (W = 4) at distance
 // r_t = first + t + 1/2 - X. For the cosine kernel the four values are
 // 1/4 (1 + cos th), 1/4 (1 - sin th), 1/4 (1 - cos th), 1/4 (1 + sin th) with
@@ -370,47 +360,6 @@ __device__ __forceinline__ void axis_taps(double X, int n, int periodic, Taps<W,
       // particle, so every field read there is one the step has written
       t.idx[i] = in ? k : (k < 0 ? 0 : n - 1);
       if (!in) t.w[i] = WT(0);
-      s += t.w[i];
-    }
-#pragma unroll
-    for (int i = 0; i < W; ++i) t.w[i] /= s;
-  }
-}
-
-// The same taps from a particle's cell c and FP32 offset f inside it (X = c + f),
-// all in FP32 and integer arithmetic: floor(X - 1/2) = c + floor(f - 1/2) and
-// r_0 = (first - c) + 1/2 - f.
-template <int W>
-__device__ __forceinline__ void axis_taps_local(int c, float f, int n, int periodic,
-                                                Taps<W, float>& t) {
-  const int b = c + (int)floorf(f - 0.5f);
-  t.first = (W == 2) ? b : b - 1;
-  const float r0 = (float)(t.first - c) + 0.5f - f;
-  if constexpr (W == 2) {
-    t.w[0] = 1.f + r0;
-    t.w[1] = -r0;
-  } else {
-    float sn, cs;
-    sincospif(0.5f * r0, &sn, &cs);
-    t.w[0] = 0.25f * (1.f + cs);
-    t.w[1] = 0.25f * (1.f - sn);
-    t.w[2] = 0.25f * (1.f - cs);
-    t.w[3] = 0.25f * (1.f + sn);
-  }
-  if (periodic) {
-#pragma unroll
-    for (int i = 0; i < W; ++i) {
-      int k = (t.first + i) % n;
-      t.idx[i] = k < 0 ? k + n : k;
-    }
-  } else {
-    float s = 0.f;
-#pragma unroll
-    for (int i = 0; i < W; ++i) {
-      int k = t.first + i;
-      bool in = (k >= 0 && k < n);
-      t.idx[i] = in ? k : (k < 0 ? 0 : n - 1);
-      if (!in) t.w[i] = 0.f;
       s += t.w[i];
     }
 #pragma unroll
@@ -532,6 +481,7 @@ struct CoupleArgs {
   float xf_margin;      // bound on the FP32 rounding error of a distance
   double* gout;      // [d][np] by slot
   double* Fcout;     // [d][np] by slot
+  float* Fcf;        // [d][np] by slot, FP32 copy of Fcout (32- and 16-bit storage), or null
   double* rl;        // sub-cycling: [np] rho_l by slot
   double* jl;        // sub-cycling: [d][np] j_l by slot
   double* Fs;        // sub-cycling: [d][np] contact force of the sub-step by slot
@@ -745,6 +695,11 @@ __global__ void __launch_bounds__(256) k_contacts(CoupleArgs A) {
   }
 #pragma unroll
   for (int k = 0; k < D; ++k) (SUB ? A.Fs : A.Fcout)[k * np + sl] = Fc[k];
+  if (!SUB && A.Fcf) {
+    // most particles touch nothing: their zero needs no FP64 conversion
+#pragma unroll
+    for (int k = 0; k < D; ++k) A.Fcf[k * np + sl] = Fc[k] != 0.0 ? (float)Fc[k] : 0.f;
+  }
 }
 
 // Shape of the moment kernel: cells per thread (as many loads in flight as the
@@ -980,8 +935,34 @@ __device__ __forceinline__ void gather_moments(const CoupleArgs& A, const Taps<W
   }
 }
 
+// One row of a 2D FP32 stencil whose W cells are consecutive (no wall drop, no
+// wrap): the force of two neighbouring cells (Fx, Fy, Fx, Fy) is one 16-byte
+// vector atomic when the first of them has an even index, so a row takes W/2
+// atomics (aligned) or W/2 + 1 (one lone cell at each end), and so fewer L1
+// sector requests than one atomic per cell.
+template <int W>
+__device__ __forceinline__ void spread_row_pairs(float* __restrict__ F, long long c0,
+                                                 const float (&wt)[W], float ax, float ay) {
+  float2* F2 = reinterpret_cast<float2*>(F);
+  float4* F4 = reinterpret_cast<float4*>(F);
+  int i = 0;
+  if (c0 & 1) {
+    atomicAdd(F2 + c0, make_float2(ax * wt[0], ay * wt[0]));
+    i = 1;
+  }
+#pragma unroll
+  for (int k = 0; k < W / 2; ++k) {
+    const int j = i + 2 * k;
+    if (j + 1 < W)
+      atomicAdd(F4 + ((c0 + j) >> 1),
+                make_float4(ax * wt[j], ay * wt[j], ax * wt[j + 1], ay * wt[j + 1]));
+  }
+  if (c0 & 1) atomicAdd(F2 + c0 + W - 1, make_float2(ax * wt[W - 1], ay * wt[W - 1]));
+}
+
 // Eq. (9): add amp * w to F at every tap (one vector atomic per cell in FP32,
-// one atomic per component in FP64).
+// one atomic per component in FP64; in 2D FP32, rows of consecutive cells by
+// pairs of cells).
 template <int D, int W, typename TW, typename FT>
 __device__ __forceinline__ void spread_amp(const CoupleArgs& A, const Taps<W, TW>& tx,
                                            const Taps<W, TW>& ty, const Taps<W, TW>& tz,
@@ -989,6 +970,21 @@ __device__ __forceinline__ void spread_amp(const CoupleArgs& A, const Taps<W, TW
   constexpr int WZ = D == 3 ? W : 1;
   const Geometry& g = A.g;
   FT* F = (FT*)A.F;
+  if constexpr (D == 2 && sizeof(FT) == 4) {
+    if (tx.idx[W - 1] == tx.idx[0] + (W - 1)) {  // consecutive: no dropped node, no wrap
+#pragma unroll
+      for (int iy = 0; iy < W; ++iy) {
+        const FT wyz = (FT)ty.w[iy];
+        if (wyz == FT(0)) continue;
+        float wt[W];
+#pragma unroll
+        for (int ix = 0; ix < W; ++ix) wt[ix] = (FT)tx.w[ix] * wyz;
+        spread_row_pairs<W>((float*)F, (long long)ty.idx[iy] * g.n[0] + tx.idx[0], wt, amp[0],
+                            amp[1]);
+      }
+      return;
+    }
+  }
 #pragma unroll 1
   for (int iz = 0; iz < WZ; ++iz) {
     FT wz = FT(1);
@@ -1082,7 +1078,7 @@ template <int D, class St, typename FT>
 __device__ __forceinline__ void advance_particle(const CoupleArgs& A, long long sl, unsigned p,
                                                  const int4& mc, const float4& mf,
                                                  const double (&X)[3], const double (&U)[3],
-                                                 const double (&Fc)[3], typename St::R rs,
+                                                 const typename St::R (&Fc)[3], typename St::R rs,
                                                  const typename St::R (&js)[3], FT (&amp)[3]) {
   using R = typename St::R;
   const Geometry& g = A.g;
@@ -1125,14 +1121,14 @@ __device__ __forceinline__ void advance_particle(const CoupleArgs& A, long long 
       const float inv = 1.f / (cc.x + 2.f * cc.y * rho);
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        dU[k] = (2.f * cc.y * (js[k] - rho * Uf[k]) + cc.z * A.ph.gravityf[k] + (float)Fc[k]) * inv;
+        dU[k] = (2.f * cc.y * (js[k] - rho * Uf[k]) + cc.z * A.ph.gravityf[k] + Fc[k]) * inv;
         Ub[k] = Uf[k] + dU[k];
       }
     } else {
       const float invm = 1.f / cc.x;
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        dU[k] = (cc.z * A.ph.gravityf[k] + (float)Fc[k] - 2.f * cc.y * (rho * Uf[k] - js[k])) * invm;
+        dU[k] = (cc.z * A.ph.gravityf[k] + Fc[k] - 2.f * cc.y * (rho * Uf[k] - js[k])) * invm;
         Ub[k] = Uf[k];
       }
     }
@@ -1219,13 +1215,15 @@ __global__ void __launch_bounds__(256, sizeof(typename St::R) == 4 ? (Lattice<Q>
     // The 2D FP32-storage taps come from the cell record alone; loading the
     // particle state after the gathers keeps it out of their registers.
     constexpr bool LATE = D == 2 && sizeof(R) == 4;
-    double U[3] = {0.0, 0.0, 0.0}, Fc[3] = {0.0, 0.0, 0.0};
+    double U[3] = {0.0, 0.0, 0.0};
+    R Fc[3] = {R(0), R(0), R(0)};
     auto load_state = [&]() {
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         X[k] = A.X[k * np + p];
         U[k] = A.U[k * np + p];
-        Fc[k] = A.Fcout[k * np + sl];
+        if constexpr (sizeof(R) == 8) Fc[k] = A.Fcout[k * np + sl];
+        else Fc[k] = A.Fcf[k * np + sl];
       }
     };
     if constexpr (!LATE) load_state();
@@ -1244,6 +1242,16 @@ __global__ void __launch_bounds__(256, sizeof(typename St::R) == 4 ? (Lattice<Q>
   if constexpr (LAG) {
     Taps<W, R> sx, sy, sz;
     particle_taps<D, W, false, R>(g, mc, mf, X, sx, sy, sz);
+    if (A.spread) spread_amp<D, W, R, FT>(A, sx, sy, sz, amp);
+    else keep_taps<D, W, R>(A, sl, sx, sy, sz);
+  } else if constexpr (sizeof(R) == 4) {
+    // FP32 taps come from the sorted record alone: recomputing them after the
+    // update (from a fresh read of the record, which the stores above may alias)
+    // costs a few FP32 operations and keeps them out of the registers the update
+    // needs
+    const float4 mf2 = A.xs[sl];
+    Taps<W, R> sx, sy, sz;
+    particle_taps<D, W, false, R>(g, mc, mf2, X, sx, sy, sz);
     if (A.spread) spread_amp<D, W, R, FT>(A, sx, sy, sz, amp);
     else keep_taps<D, W, R>(A, sl, sx, sy, sz);
   } else {
@@ -1617,6 +1625,7 @@ CoupleArgs couple_args(const State& s) {
   A.xf_margin = 1e-5f;
   A.gout = P.g;
   A.Fcout = P.Fc;
+  A.Fcf = s.precision == PIBM_FP64 ? nullptr : P.Fcf;
   A.rl = P.rl;
   A.jl = P.jl;
   A.Fs = P.Fs;

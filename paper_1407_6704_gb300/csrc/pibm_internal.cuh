@@ -315,6 +315,7 @@ struct Particles {
   int4* cs[2];    // cell (x, y, z) and storage position
   double* g;      // [d][np] force density of the last step (Eq. 7), by slot of that step
   double* Fc;     // [d][np] contact force of the last step, by slot of that step
+  float* Fcf;     // [d][np] the same in FP32 (32- and 16-bit storage: the FP32 update reads it)
   // DEM sub-cycling scratch, by slot (allocated when substeps > 1)
   double* rl;     // [np] interpolated rho_l of the step
   double* jl;     // [d][np] interpolated j_l of the step
@@ -402,6 +403,62 @@ __device__ __forceinline__ double min_image(double s, int n, int periodic) {
 }
 
 // ---------------------------------------------------------------------------
+// Delta weights along one axis (Eqs. 10-11 and the 2-point hat), shared by the
+// particle kernels and the collision that gathers the spread force, so that both
+// apply bit-identical weights.
+// ---------------------------------------------------------------------------
+template <int W, typename WT>
+struct Taps {
+  int first;    // unwrapped index of the first node
+  int idx[W];   // wrapped (periodic) or clamped (dropped wall node) index
+  WT w[W];
+};
+
+__device__ __forceinline__ void sincospi_t(double a, double* s, double* c) { sincospi(a, s, c); }
+__device__ __forceinline__ void sincospi_t(float a, float* s, float* c) { sincospif(a, s, c); }
+
+// The same taps from a particle's cell c and FP32 offset f inside it (X = c + f),
+// all in FP32 and integer arithmetic: floor(X - 1/2) = c + floor(f - 1/2) and
+// r_0 = (first - c) + 1/2 - f.
+template <int W>
+__device__ __forceinline__ void axis_taps_local(int c, float f, int n, int periodic,
+                                                Taps<W, float>& t) {
+  const int b = c + (int)floorf(f - 0.5f);
+  t.first = (W == 2) ? b : b - 1;
+  const float r0 = (float)(t.first - c) + 0.5f - f;
+  if constexpr (W == 2) {
+    t.w[0] = 1.f + r0;
+    t.w[1] = -r0;
+  } else {
+    float sn, cs;
+    sincospif(0.5f * r0, &sn, &cs);
+    t.w[0] = 0.25f * (1.f + cs);
+    t.w[1] = 0.25f * (1.f - sn);
+    t.w[2] = 0.25f * (1.f - cs);
+    t.w[3] = 0.25f * (1.f + sn);
+  }
+  if (periodic) {
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      int k = (t.first + i) % n;
+      t.idx[i] = k < 0 ? k + n : k;
+    }
+  } else {
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      int k = t.first + i;
+      bool in = (k >= 0 && k < n);
+      t.idx[i] = in ? k : (k < 0 ? 0 : n - 1);
+      if (!in) t.w[i] = 0.f;
+      s += t.w[i];
+    }
+#pragma unroll
+    for (int i = 0; i < W; ++i) t.w[i] /= s;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers (defined in lbm.cu, particles.cu, reduce.cu)
 // ---------------------------------------------------------------------------
 // Fluid: one fused pull-stream + Guo-forced BGK collision, f[cur] -> f[1-cur];
@@ -415,6 +472,7 @@ bool collide_uses_pair_kernel(const State& s);
 // cell once. Available for 32- and 64-bit storage.
 bool collide_tiles_supported(const State& s);
 cudaError_t launch_collide_tiles(const State& s, cudaStream_t st, int which, int grid);
+
 // Write plane a of the stored buffer f[cur] from FP64 values src (already
 // un-streamed by the host), or from the rest value w_a when src is NULL.
 cudaError_t launch_store_plane(const State& s, int a, const double* src, cudaStream_t st);
@@ -446,6 +504,9 @@ struct HandleView {
   cudaStream_t stream;
 };
 HandleView handle_view(pibm_t* h);
+
+// Record a failed CUDA call for pibm_last_error (this thread).
+void record_cuda_error(const char* what, cudaError_t e);
 
 // Gradient of the mean settling velocity by the discrete adjoint (adjoint.cu).
 int settling_gradient(const pibm_config* cfg, int64_t nsteps, int64_t K, void* stream,

@@ -162,3 +162,14 @@ def test_empty_particle_set_is_valid(lib):
     c.n_particles = 0
     st, n = _ws(lib, c)
     assert st == 0 and n > 0
+
+
+def test_noalloc_size_check_cannot_overflow(lib):
+    """Extents whose product overflows 64 bits are rejected as too big. The size
+    check comes before any CUDA call, so this needs no GPU and the pointers are
+    never dereferenced."""
+    dummy = ctypes.c_void_p(256)
+    for q, n in [(9, (2**63 - 1, 1, 1)), (9, (5000, 2**62, 1)), (19, (16, 2**60, 16)),
+                 (19, (4096, 4096, 2**62)), (15, (1, 1, 2**63 - 1))]:
+        n3 = (ctypes.c_int64 * 3)(*n)
+        assert lib.pibm_fluid_sums_noalloc(dummy, q, n3, dummy, None) == _lib.PIBM_ETOOBIG, n

@@ -2,8 +2,11 @@
 state it reports (populations, positions and velocities from pibm_read_fields,
 passed to pibm_create as f0, x0 and u0) continues as the uninterrupted run. The
 step keeps no other history: linear contacts have none, and g and the contact
-forces are recomputed every step. FP64, the parity bar of 1e-10 (the spreading's
-atomics order the sums differently run to run)."""
+forces are recomputed every step. FP64, the parity bar of 1e-10 relative: positions
+and velocities relative to the largest displacement and speed, populations relative
+to their largest deviation from the rest state w (the part of f that the run
+changes; f itself is about 0.1 everywhere). The spreading's atomics may order the
+sums differently run to run; on GB300 the difference measured zero."""
 import numpy as np
 import pytest
 
@@ -49,4 +52,4 @@ def test_restart_from_the_read_state_continues_the_run(q, n, periodic, rebin):
     dx = np.abs(got["x"] - whole["x"]).max() / np.abs(whole["x"] - c["X"]).max()
     du = np.abs(got["u"] - whole["u"]).max() / np.abs(whole["u"]).max()
     print("restart", q, dpop, dx, du)
-    assert dpop < 1e-8 and dx < 1e-10 and du < 1e-10
+    assert dpop < 1e-10 and dx < 1e-10 and du < 1e-10
