@@ -53,9 +53,10 @@ extern "C" {
 #define PIBM_EINVAL (-1)    /* bad argument or configuration */
 #define PIBM_ENOMEM (-2)    /* workspace too small or allocation failed */
 #define PIBM_ECUDA (-3)     /* a CUDA call failed */
-#define PIBM_EUNSTABLE (-4) /* non-finite fluid or particle state detected, or a particle
-                               moved farther than the cell list allows (sub-cycling,
-                               rebin_every > 1) */
+#define PIBM_EUNSTABLE (-4) /* non-finite fluid or particle state detected, a fluid speed
+                               above 0.3 lattice units (Mach guard: the equilibrium of
+                               Eq. 3 is a low-Mach expansion), or a particle moved farther
+                               than the cell list allows (sub-cycling, rebin_every > 1) */
 #define PIBM_EESCAPED (-5)  /* a particle crossed a wall */
 #define PIBM_ENOTSUP (-6)   /* combination not built into this library */
 #define PIBM_EINTERNAL (-7) /* a device-side index check failed; the access was skipped */
@@ -95,7 +96,7 @@ extern "C" {
 
 /* storage / arithmetic of the populations; particles, contacts and the
  * particle integration are FP64 in every mode */
-#define PIBM_FP64 0 /* populations, collision and spread force in FP64 */
+#define PIBM_FP64 0 /* populations stored as f - w in FP64, FP64 collision and force */
 #define PIBM_FP32 1 /* populations stored as f - w in FP32, FP32 collision and force field */
 #define PIBM_FP16 2 /* populations stored as (f - w) * 2^12 in FP16, FP32 collision and force */
 #define PIBM_BF16 3 /* populations stored as f - w in BF16, FP32 collision and force field */
@@ -194,9 +195,10 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
  * (whole cell-list rebuild periods are replayed from CUDA graphs). With overlap
  * the work of each step forks onto a second stream of the handle and joins back
  * before the step ends, so the handle's stream orders everything after it.
- * Health flags raised on the device (non-finite state, escaped particle, a
- * particle beyond the skin of a kept cell list) are reported by the next
- * synchronising call; after such a flag the state is not meaningful. */
+ * Health flags raised on the device (non-finite state, a fluid speed above the
+ * Mach guard, escaped particle, a particle beyond the skin of a kept cell list)
+ * are reported by the next synchronising call; after such a flag the state is
+ * not meaningful. */
 int pibm_step(pibm_t* h, int64_t nsteps);
 
 /* Per-particle forces of the last step, AoS [n_particles][d] FP64:

@@ -5,7 +5,9 @@ baseline leg use this module. It loads ``liboracle.so`` (built from
 ``pibm_oracle.c``) and never touches the CUDA library.
 
 Arrays follow the C-ABI layouts: populations ``(q, nz, ny, nx)`` (``(q, ny, nx)``
-in 2D), force ``(d, ...)``, particle vectors AoS ``(n_particles, d)``.
+in 2D), force ``(d, ...)``, particle vectors AoS ``(n_particles, d)``. The C code
+keeps populations as g = f - w (see ``pibm_oracle.c``); this module converts at
+its boundary, so every population array it takes or returns holds f itself.
 """
 import ctypes
 import os
@@ -14,7 +16,7 @@ import numpy as np
 
 from . import build as _build
 
-_lib = None
+_libs = {}
 
 
 class OrParams(ctypes.Structure):
@@ -38,10 +40,10 @@ class OrParams(ctypes.Structure):
     ]
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        path = _build.build()
+def lib(parallel=False):
+    """The serial oracle library, or (parallel=True) its OpenMP build."""
+    if parallel not in _libs:
+        path = _build.build(parallel=parallel)
         L = ctypes.CDLL(path)
         P = ctypes.POINTER(OrParams)
         dp = ctypes.POINTER(ctypes.c_double)
@@ -65,8 +67,8 @@ def lib():
         L.or_run.argtypes = [P, ctypes.c_long] + step_args[1:]
         L.or_force_at_cell.argtypes = [P, dp, ctypes.c_long, dp, dp, dp, dp, ctypes.c_long, dp]
         L.or_cell_after_step.argtypes = [P, dp, ctypes.c_long, dp, dp, dp, dp, ctypes.c_long, dp]
-        _lib = L
-    return _lib
+        _libs[parallel] = L
+    return _libs[parallel]
 
 
 def _p(a):
@@ -100,11 +102,13 @@ class Oracle:
                  gravity=(0.0, 0.0, 0.0), kn=1e-2, restitution=0.9,
                  x0=None, u0=None, diameter=None, density_ratio=None, f0=None,
                  interp="delta", contact="linear", young=1.0, poisson=0.3, wall_young=None,
-                 wall_poisson=None, substeps=1):
+                 wall_poisson=None, substeps=1, parallel=False):
         """interp: "delta" (the spreading kernel) or "lagrange4" (Eq. 5);
         contact: "linear" (k_n, e) or "hertz" (Eq. 15 with young/poisson of the
         particles and of the walls, default the particles' material, and e);
-        substeps: DEM sub-steps per fluid step."""
+        substeps: DEM sub-steps per fluid step; parallel: whole steps run in the
+        OpenMP build (bitwise identical results, all cores)."""
+        self.parallel = bool(parallel)
         self.q = int(q)
         self.d, self.e, self.w, self.opp = lattice(self.q)
         n = list(n) + [1] * (3 - len(n))
@@ -124,14 +128,13 @@ class Oracle:
         self.substeps = int(substeps)
         self.shape = (n[1], n[0]) if self.d == 2 else (n[2], n[1], n[0])
         self.ncell = n[0] * n[1] * n[2]
+        self._wb = self.w.reshape((-1,) + (1,) * len(self.shape))
         if f0 is None:
-            f = np.empty((self.q,) + self.shape)
-            for a in range(self.q):
-                f[a] = self.w[a]
+            g = np.zeros((self.q,) + self.shape)  # the rest state f = w
         else:
-            f = np.array(f0, dtype=np.float64, copy=True).reshape((self.q,) + self.shape)
-        self.f = np.ascontiguousarray(f)
-        self.fs = np.zeros_like(self.f)
+            g = np.asarray(f0, dtype=np.float64).reshape((self.q,) + self.shape) - self._wb
+        self.fdev = np.ascontiguousarray(g)  # stored populations minus w, advanced by step()
+        self.fs = np.zeros_like(self.fdev)
         self.F = np.zeros((self.d,) + self.shape)
         np_ = 0 if x0 is None else len(x0)
         self.np = np_
@@ -147,10 +150,24 @@ class Oracle:
         self.Fc = np.zeros_like(self.X)
         self.diag = np.zeros(2)
 
+    @property
+    def f(self):
+        """Post-stream populations of the current state (a new array)."""
+        return self.fdev + self._wb
+
+    @f.setter
+    def f(self, value):
+        self.fdev = np.ascontiguousarray(np.asarray(value, dtype=np.float64).reshape(self.fdev.shape)
+                                      - self._wb)
+
+    def _to_g(self, f):
+        return np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(self.fdev.shape)
+                                    - self._wb)
+
     # --- whole steps -------------------------------------------------------
     def step(self, nsteps=1):
-        L = lib()
-        L.or_run(ctypes.byref(self.params), int(nsteps), _p(self.f), _p(self.fs), _p(self.F),
+        L = lib(self.parallel)
+        L.or_run(ctypes.byref(self.params), int(nsteps), _p(self.fdev), _p(self.fs), _p(self.F),
                  self.np, _p(self.X), _p(self.U), _p(self.dia), _p(self.rr), _p(self.Xn),
                  _p(self.Un), _p(self.g), _p(self.Fc), _p(self.diag))
 
@@ -162,10 +179,10 @@ class Oracle:
 
     # --- pieces --------------------------------------------------------------
     def moments(self, f=None):
-        f = self.f if f is None else np.ascontiguousarray(f, dtype=np.float64)
+        g = self.fdev if f is None else self._to_g(f)
         rho = np.zeros(self.shape)
         j = np.zeros((self.d,) + self.shape)
-        lib().or_moments(ctypes.byref(self.params), _p(f), _p(rho), _p(j))
+        lib().or_moments(ctypes.byref(self.params), _p(g), _p(rho), _p(j))
         return rho, j
 
     def taps(self, axis, X):
@@ -184,9 +201,9 @@ class Oracle:
 
     def interp_pops(self, X):
         X = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(self.d))
-        fl = np.zeros(self.q)
-        lib().or_interp_pops(ctypes.byref(self.params), _p(self.f), _p(X), _p(fl))
-        return fl
+        gl = np.zeros(self.q)
+        lib().or_interp_pops(ctypes.byref(self.params), _p(self.fdev), _p(X), _p(gl))
+        return gl + self.w
 
     def contact_force(self, i):
         Fc = np.zeros(self.d)
@@ -199,23 +216,23 @@ class Oracle:
         assert self.substeps <= 1, "sampled evaluation covers steps without sub-cycling"
         Xn, Un, g, Fc = (np.zeros(self.d) for _ in range(4))
         dv = np.zeros(1)
-        esc = lib().or_particle_update(ctypes.byref(self.params), _p(self.f), self.np, _p(self.X),
+        esc = lib().or_particle_update(ctypes.byref(self.params), _p(self.fdev), self.np, _p(self.X),
                                        _p(self.U), _p(self.dia), _p(self.rr), int(i), _p(Xn),
                                        _p(Un), _p(g), _p(Fc), _p(dv))
         return Xn, Un, g, Fc, float(dv[0]), bool(esc)
 
     def collide(self, f, F):
-        f = np.ascontiguousarray(f, dtype=np.float64)
+        g = self._to_g(f)
         F = np.ascontiguousarray(F, dtype=np.float64)
-        out = np.zeros_like(f)
-        lib().or_collide(ctypes.byref(self.params), _p(f), _p(F), _p(out))
-        return out
+        out = np.zeros_like(g)
+        lib().or_collide(ctypes.byref(self.params), _p(g), _p(F), _p(out))
+        return out + self._wb
 
     def stream(self, fs):
-        fs = np.ascontiguousarray(fs, dtype=np.float64)
-        out = np.zeros_like(fs)
-        lib().or_stream(ctypes.byref(self.params), _p(fs), _p(out))
-        return out
+        gs = self._to_g(fs)
+        out = np.zeros_like(gs)
+        lib().or_stream(ctypes.byref(self.params), _p(gs), _p(out))
+        return out + self._wb
 
     def spread_one(self, X, dia, g, F):
         X = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(self.d))
@@ -226,13 +243,13 @@ class Oracle:
     def force_at_cell(self, cell):
         assert self.substeps <= 1, "sampled evaluation covers steps without sub-cycling"
         out = np.zeros(self.d)
-        lib().or_force_at_cell(ctypes.byref(self.params), _p(self.f), self.np, _p(self.X),
+        lib().or_force_at_cell(ctypes.byref(self.params), _p(self.fdev), self.np, _p(self.X),
                                _p(self.U), _p(self.dia), _p(self.rr), int(cell), _p(out))
         return out
 
     def cell_after_step(self, cell):
         assert self.substeps <= 1, "sampled evaluation covers steps without sub-cycling"
         out = np.zeros(self.q)
-        lib().or_cell_after_step(ctypes.byref(self.params), _p(self.f), self.np, _p(self.X),
+        lib().or_cell_after_step(ctypes.byref(self.params), _p(self.fdev), self.np, _p(self.X),
                                  _p(self.U), _p(self.dia), _p(self.rr), int(cell), _p(out))
-        return out
+        return out + self.w

@@ -44,8 +44,26 @@
  *    times with h = 1/S, and the fluid receives the time average of the force
  *    density; S = 1 is the plain step.
  *
- * Layouts: populations f[a * ncell + c], c = x + nx * (y + ny * z);
+ * Stored populations: every array of populations holds g_a = f_a - w_a, the
+ * deviation from the rest state (f_a = w_a, rho = 1, u = 0), with w_a the exact
+ * weights of the velocity set. This is the same method with f = w + g
+ * substituted: the rest state is a fixed point of Eqs. (2), (3) and (8) with
+ * zero force, and of streaming (w_a is constant across the lattice and equal
+ * for opposite directions), so g obeys the same update with
+ * g^eq_a = f^eq_a - w_a = w_a [(rho - 1) + rho (3 e.u + 4.5 (e.u)^2 - 1.5 u^2)],
+ * rho = 1 + sum_a g_a and j = sum_a e_a g_a. Only the rounding differs: in a weakly
+ * driven flow f is about w while the flow lives in g, so every step rounds at the
+ * scale of g rather than of w.
+ *
+ * Layouts: populations g[a * ncell + c], c = x + nx * (y + ny * z);
  * force F[k * ncell + c]; particle vectors are AoS with d components.
+ *
+ * Threads: built with -fopenmp, the loops over cells and the per-particle
+ * updates (each reads the step-n state and writes only its own particle's
+ * results) run in parallel; the spreading, whose sums into shared cells fix the
+ * summation order, stays serial in particle index order. Every value is then
+ * computed by the same operations as in the serial build, so the two builds give
+ * bitwise identical results (a test checks this).
  */
 #include <math.h>
 #include <stdint.h>
@@ -216,11 +234,13 @@ int or_interp_taps(const or_params* p, int axis, double X, int* idx, double* w) 
   return or_taps(p, axis, X, idx, w);
 }
 
-/* Macroscopic moments of the stored populations: rho = sum f, j = sum e f. */
+/* Macroscopic moments of the stored populations g = f - w: rho = sum f =
+ * 1 + sum g, j = sum e f = sum e g. */
 void or_moments(const or_params* p, const double* f, double* rho, double* j) {
   or_lattice_t L;
   or_lattice_get(p->q, &L);
   long nc = or_ncell(p);
+#pragma omp parallel for schedule(static)
   for (long c = 0; c < nc; ++c) {
     double r = 0.0, m[3] = {0.0, 0.0, 0.0};
     for (int a = 0; a < L.q; ++a) {
@@ -228,13 +248,14 @@ void or_moments(const or_params* p, const double* f, double* rho, double* j) {
       r += v;
       for (int k = 0; k < L.d; ++k) m[k] += L.e[a][k] * v;
     }
-    rho[c] = r;
+    rho[c] = 1.0 + r;
     for (int k = 0; k < L.d; ++k) j[k * nc + c] = m[k];
   }
 }
 
 /* Eq. (4): every population interpolated to the particle position X with the
- * tensor-product weights of the per-axis interpolation taps. */
+ * tensor-product weights of the per-axis interpolation taps, on the stored
+ * deviations g = f - w (the weights sum to one, so f(X) = w + g(X)). */
 void or_interp_pops(const or_params* p, const double* f, const double* X, double* fl) {
   or_lattice_t L;
   or_lattice_get(p->q, &L);
@@ -348,12 +369,13 @@ int or_particle_update(const or_params* p, const double* f, long np, const doubl
   or_lattice_get(p->q, &L);
   int d = L.d;
   double fl[OR_MAXQ];
-  or_interp_pops(p, f, X + i * d, fl); /* Eq. (4) */
-  double rho_l = 0.0, j_l[3] = {0.0, 0.0, 0.0};
+  or_interp_pops(p, f, X + i * d, fl); /* Eq. (4), fl = f(X_l) - w */
+  double sum_l = 0.0, j_l[3] = {0.0, 0.0, 0.0};
   for (int a = 0; a < L.q; ++a) {
-    rho_l += fl[a];
+    sum_l += fl[a];
     for (int k = 0; k < d; ++k) j_l[k] += L.e[a][k] * fl[a];
   }
+  double rho_l = 1.0 + sum_l;
   or_contact_force(p, np, X, U, dia, rr, i, Fc);
   double m = or_mass(d, dia[i], rr[i]);
   double Ap = OR_PI * dia[i] * dia[i] / 4.0;
@@ -372,7 +394,9 @@ int or_particle_update(const or_params* p, const double* f, long np, const doubl
     }
   }
   /* Eq. (6): population bounced into beta = opposite(alpha) by the moving
-   * particle; Eq. (7): momentum exchanged, sum_beta e_beta (new - old). */
+   * particle; Eq. (7): momentum exchanged, sum_beta e_beta (new - old). Both
+   * sides are taken minus w (w_alpha = w_beta), which leaves the differences
+   * unchanged. */
   double fnew[OR_MAXQ];
   for (int a = 0; a < L.q; ++a) {
     double eu = 0.0;
@@ -426,16 +450,17 @@ void or_spread_one(const or_params* p, const double* X, double dia, const double
 }
 
 /* Collision of one cell, Eqs. (2), (3), (8): u = (j + F/2) / rho, equilibrium,
- * Guo body-force term, relaxation. fc: the q populations of the cell (in),
- * Fc: the d force components, out: post-collision populations. */
+ * Guo body-force term, relaxation. fc: the q stored populations g = f - w of the
+ * cell (in), Fc: the d force components, out: post-collision g. */
 static void or_collide_cell(const or_lattice_t* L, double tau, const double* fc, const double* Fc,
                             double* out) {
   int d = L->d;
-  double rho = 0.0, j[3] = {0.0, 0.0, 0.0}, u[3] = {0.0, 0.0, 0.0};
+  double sum = 0.0, j[3] = {0.0, 0.0, 0.0}, u[3] = {0.0, 0.0, 0.0};
   for (int a = 0; a < L->q; ++a) {
-    rho += fc[a];
+    sum += fc[a];
     for (int k = 0; k < d; ++k) j[k] += L->e[a][k] * fc[a];
   }
+  double rho = 1.0 + sum;
   double uu = 0.0;
   for (int k = 0; k < d; ++k) {
     u[k] = (j[k] + 0.5 * Fc[k]) / rho;
@@ -448,7 +473,8 @@ static void or_collide_cell(const or_lattice_t* L, double tau, const double* fc,
       eF += L->e[a][k] * Fc[k];
       emuF += (L->e[a][k] - u[k]) * Fc[k];
     }
-    double feq = rho * L->w[a] * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+    /* f^eq - w = w [(rho - 1) + rho (3 eu + 4.5 eu^2 - 1.5 uu)], rho - 1 = sum */
+    double feq = L->w[a] * (sum + rho * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
     double Fb = (1.0 - 1.0 / (2.0 * tau)) * L->w[a] * (3.0 * emuF + 9.0 * eu * eF);
     out[a] = fc[a] - (fc[a] - feq) / tau + Fb;
   }
@@ -458,8 +484,9 @@ void or_collide(const or_params* p, const double* f, const double* F, double* fs
   or_lattice_t L;
   or_lattice_get(p->q, &L);
   long nc = or_ncell(p);
-  double fc[OR_MAXQ], out[OR_MAXQ], Fc[3];
+#pragma omp parallel for schedule(static)
   for (long c = 0; c < nc; ++c) {
+    double fc[OR_MAXQ], out[OR_MAXQ], Fc[3];
     for (int a = 0; a < L.q; ++a) fc[a] = f[a * nc + c];
     for (int k = 0; k < L.d; ++k) Fc[k] = F ? F[k * nc + c] : 0.0;
     or_collide_cell(&L, p->tau, fc, Fc, out);
@@ -489,18 +516,18 @@ void or_stream(const or_params* p, const double* fs, double* f) {
   or_lattice_t L;
   or_lattice_get(p->q, &L);
   long nc = or_ncell(p);
-  int x[3], src[3];
-  for (x[2] = 0; x[2] < p->n[2]; ++x[2])
-    for (x[1] = 0; x[1] < p->n[1]; ++x[1])
-      for (x[0] = 0; x[0] < p->n[0]; ++x[0]) {
-        long c = or_cell(p, x);
-        for (int a = 0; a < L.q; ++a) {
-          if (or_source(p, &L, x, a, src))
-            f[a * nc + c] = fs[L.opp[a] * nc + c];
-          else
-            f[a * nc + c] = fs[a * nc + or_cell(p, src)];
-        }
-      }
+#pragma omp parallel for schedule(static)
+  for (long c = 0; c < nc; ++c) {
+    int x[3] = {(int)(c % p->n[0]), (int)((c / p->n[0]) % p->n[1]),
+                (int)(c / ((long)p->n[0] * p->n[1]))};
+    int src[3];
+    for (int a = 0; a < L.q; ++a) {
+      if (or_source(p, &L, x, a, src))
+        f[a * nc + c] = fs[L.opp[a] * nc + c];
+      else
+        f[a * nc + c] = fs[a * nc + or_cell(p, src)];
+    }
+  }
 }
 
 /* One full step in the order stated at the top of this file. f is advanced
@@ -533,22 +560,26 @@ static double or_particles_subcycled(const or_params* p, const double* f, long n
   double* Us = (double*)malloc(sizeof(double) * np * d);
   double* Fs = (double*)malloc(sizeof(double) * np * d);
   double esc = 0.0;
+#pragma omp parallel for schedule(static)
   for (long i = 0; i < np; ++i) {
     double fl[OR_MAXQ];
     or_interp_pops(p, f, X + i * d, fl);
-    rho[i] = 0.0;
+    double sum_l = 0.0;
     for (int k = 0; k < d; ++k) jl[i * d + k] = 0.0;
     for (int a = 0; a < L.q; ++a) {
-      rho[i] += fl[a];
+      sum_l += fl[a];
       for (int k = 0; k < d; ++k) jl[i * d + k] += L.e[a][k] * fl[a];
     }
+    rho[i] = 1.0 + sum_l;
   }
   memcpy(Xs, X, sizeof(double) * np * d);
   memcpy(Us, U, sizeof(double) * np * d);
   memset(g, 0, sizeof(double) * np * d);
   memset(Fc, 0, sizeof(double) * np * d);
   for (int sub = 0; sub < S; ++sub) {
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < np; ++i) or_contact_force(p, np, Xs, Us, dia, rr, i, Fs + i * d);
+#pragma omp parallel for schedule(static) reduction(+ : esc)
     for (long i = 0; i < np; ++i) {
       double m = or_mass(d, dia[i], rr[i]);
       double Ap = OR_PI * dia[i] * dia[i] / 4.0;
@@ -598,6 +629,7 @@ void or_step(const or_params* p, double* f, double* fs, double* F, long np, doub
   if (p->substeps > 1) {
     esc = or_particles_subcycled(p, f, np, X, U, dia, rr, Xn, Un, g, Fc);
   } else {
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : esc) reduction(max : dev_max)
     for (long i = 0; i < np; ++i) {
       double dv = 0.0;
       esc += or_particle_update(p, f, np, X, U, dia, rr, i, Xn + i * d, Un + i * d, g + i * d,

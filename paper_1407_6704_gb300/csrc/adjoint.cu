@@ -149,7 +149,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_collide(Geometry g, double 
     for (int a = 0; a < Q; ++a) {
       bool bb;
       const long long src = adj_pull_src<Q>(g, x, y, z, a, bb);
-      f[a] = bb ? fin[opp(a) * P + c] : fin[a * P + src];
+      // the stored value is f - S w (StoreF64 keeps the deviation from rest)
+      f[a] = (bb ? fin[opp(a) * P + c] : fin[a * P + src]) + StoreF64::S * L::w(a);
       gb[a] = gbar[a * P + c];
     }
     double Fv[3] = {0.0, 0.0, 0.0};
@@ -309,6 +310,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_update(AdjArgs A) {
       }
     }
   }
+  rho_l += StoreF64::S;  // the moment field holds rho - S, as in the forward step
   double Ubt[3], Nb[3], rlb = 0.0, jlb[3] = {0.0, 0.0, 0.0};
 #pragma unroll
   for (int k = 0; k < D; ++k) {

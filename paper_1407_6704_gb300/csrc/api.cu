@@ -322,7 +322,8 @@ int health(pibm_t* h) {
   unsigned err = 0;
   CK(cudaMemcpyAsync(&err, h->s.err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  if (err & (ERR_FLUID_NONFINITE | ERR_PARTICLE_NONFINITE | ERR_SKIN)) return PIBM_EUNSTABLE;
+  if (err & (ERR_FLUID_NONFINITE | ERR_PARTICLE_NONFINITE | ERR_SKIN | ERR_MACH))
+    return PIBM_EUNSTABLE;
   if (err & ERR_ESCAPED) return PIBM_EESCAPED;
   if (err & ERR_INDEX) return PIBM_EINTERNAL;
   return PIBM_OK;

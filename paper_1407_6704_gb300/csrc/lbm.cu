@@ -49,6 +49,13 @@ __device__ __forceinline__ bool bad_density(float r) {
   unsigned b = __float_as_uint(r);
   return (b >> 23) >= 0xffu || b == 0u;
 }
+// |u|^2 above 0.3^2 (the Mach guard: the BGK equilibrium of Eq. 3 is a low-Mach
+// expansion, c_s = 1/sqrt(3)), tested on the bit pattern of the non-negative
+// value, so that the FP64 path spends no FP64 operation on it; NaN counts too.
+__device__ __forceinline__ bool above_mach(double uu) {
+  return (unsigned long long)__double_as_longlong(uu) > 0x3FB70A3D70A3D70Aull;  // 0.09
+}
+__device__ __forceinline__ bool above_mach(float uu) { return __float_as_uint(uu) > 0x3DB851ECu; }
 __device__ __forceinline__ bool nonzero_bits(double v) { return __double_as_longlong(v) != 0; }
 __device__ __forceinline__ bool nonzero_bits(float v) { return __float_as_uint(v) != 0u; }
 
@@ -86,6 +93,7 @@ __device__ __forceinline__ void collide_cell(const typename St::R (&s)[Q],
     uu += u[k] * u[k];
     uF += u[k] * Fv[k];
   }
+  if (above_mach(uu)) atomicOr(err, ERR_MACH);
   const R om1 = R(1) - om;
   // Equilibrium minus the stored shift, Eq. (3):
   //   feq_a - S w_a = w_a sum + rho w_a (3 eu + 4.5 eu^2 - 1.5 uu)

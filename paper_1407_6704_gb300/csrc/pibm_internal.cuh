@@ -67,11 +67,15 @@ __host__ __device__ constexpr int opp(int a) { return a == 0 ? 0 : ((a & 1) ? a 
 // Population storage. The stored value is s = f - S w_a (S = 1: shifted),
 // held in type T (possibly scaled) and operated on in type R.
 // ---------------------------------------------------------------------------
-// load() turns a stored value into s (type R), store() the reverse.
+// load() turns a stored value into s (type R), store() the reverse. Every mode
+// keeps the deviation from the rest state (S = 1): the populations are about w_a
+// while the flow lives in f - w_a, so storing the deviation keeps the rounding of
+// every step at the scale of the flow (in FP64 about 1e-4 of the rounding of f
+// itself in a weakly driven flow).
 struct StoreF64 {
   using T = double;
   using R = double;
-  static constexpr int S = 0;
+  static constexpr int S = 1;
   __device__ static __forceinline__ R load(T v) { return v; }
   __device__ static __forceinline__ T store(R v) { return v; }
 };
@@ -239,6 +243,7 @@ enum : unsigned {
   ERR_ESCAPED = 4u,
   ERR_INDEX = 8u,  // an internal index check failed; the access was skipped
   ERR_SKIN = 16u,  // a particle moved farther than the cell list allows within a step
+  ERR_MACH = 32u,  // a fluid velocity above the Mach guard (|u| > 0.3 lattice units)
 };
 
 // ---------------------------------------------------------------------------

@@ -294,22 +294,29 @@ def _settling_function():
 
     class SettlingVelocity(torch.autograd.Function):
         """torch.autograd view of ``settling_gradient``: forward(tau, density_ratio,
-        x0, spec) returns the mean settling velocity as a 0-d FP64 tensor; backward
+        x0, spec) runs the forward steps only and returns the mean settling velocity
+        as a 0-d FP64 tensor; backward runs the checkpointed forward again (the run
+        is deterministic, so it repeats bit for bit) and the reverse sweep, and
         returns the adjoint gradients for tau, density_ratio and x0. ``spec`` holds
         the remaining keyword arguments of ``settling_gradient``."""
 
         @staticmethod
         def forward(ctx, tau, density_ratio, x0, spec):
-            r = settling_gradient(tau=float(tau), density_ratio=density_ratio.detach().cpu().numpy(),
-                                  x0=x0.detach().cpu().numpy(), **spec)
-            ctx.grads = (torch.tensor(r["dtau"], dtype=torch.float64),
-                         torch.from_numpy(r["drho"]), torch.from_numpy(r["dx0"]))
+            args = dict(tau=float(tau), density_ratio=density_ratio.detach().cpu().numpy(),
+                        x0=x0.detach().cpu().numpy(), **spec)
+            r = settling_gradient(grads=False, **args)
+            ctx.args = args
+            ctx.loss = r["loss"]
             return torch.tensor(r["loss"], dtype=torch.float64)
 
         @staticmethod
         def backward(ctx, grad):
-            gt, gr, gx = ctx.grads
-            return grad * gt, grad * gr, grad * gx, None
+            r = settling_gradient(**ctx.args)
+            if r["loss"] != ctx.loss:
+                raise RuntimeError("the replayed forward run differs from the first one")
+            gt = torch.tensor(r["dtau"], dtype=torch.float64)
+            return (grad * gt, grad * torch.from_numpy(r["drho"]),
+                    grad * torch.from_numpy(r["dx0"]), None)
 
     return SettlingVelocity
 

@@ -100,3 +100,58 @@ def test_autotune_keeps_the_state_and_the_results(spec):
     assert _same(_state(tuned), _state(plain))
     tuned.close()
     plain.close()
+
+
+ORACLE_SPECS = [  # (lattice, extents, periodic, tau, particles, precision, bar)
+    ("d2q9", (48, 40), (0, 0), 0.8, 60, "fp64", 1e-10),
+    ("d2q9", (40, 36), (1, 0), 0.6, 50, "fp32", 1e-4),
+    ("d2q9", (64, 32), (0, 0), 0.7, 70, "fp16", 1e-3),
+    ("d3q19", (14, 12, 16), (0, 0, 0), 0.7, 40, "fp32", 1e-4),
+]
+
+
+def test_ensemble_members_against_the_oracle():
+    """Members of different lattices and storage modes advanced together (one graph
+    launch per two steps), each compared element by element with the FP64 oracle
+    run of the same inputs: FP64 member at the FP64 bar (1e-10 relative on every
+    field, 1e-8 for populations and density against their deviation from rest);
+    FP32 at 1e-4 and FP16 at 1e-3 (relative max-norm on the velocity field and
+    the particles)."""
+    from oracle.oracle import Oracle, lattice
+    from paper_1407_6704_gb300.inputs import populations, velocities
+    from paper_1407_6704_gb300.pibm import Ensemble, Pibm
+
+    steps = 40
+    sims, refs, cases = [], [], []
+    for i, (lat, n, per, tau, npart, prec, bar) in enumerate(ORACLE_SPECS):
+        q = {"d2q9": 9, "d3q19": 19}[lat]
+        d = len(n)
+        X, dia, rr = sample_particles(n, npart, (0.3, 0.8), (1.5, 3.0), band=(0.3, 1.0),
+                                      seed=300 + i)
+        U = velocities(npart, d, seed=310 + i, scale=1e-3)
+        f0 = populations(lattice(q)[2], tuple(reversed(n)), seed=320 + i, eps=1e-3)
+        kw = dict(gravity=(0.0,) * (d - 1) + (-1e-4,), delta_width=4, x0=X, u0=U, diameter=dia,
+                  density_ratio=rr, f0=f0)
+        sims.append(Pibm(lat, n, per, tau, precision=prec, **kw))
+        ref = Oracle(q, n, per, tau, **kw)
+        ref.step(steps)
+        refs.append(ref)
+        cases.append((prec, bar, X))
+    with Ensemble(sims) as ens:
+        ens.step(steps)
+        assert ens.status() == 0
+    for sim, ref, (prec, bar, X0) in zip(sims, refs, cases):
+        got = sim.read("pop", "rho", "j", "x", "u")
+        sim.close()
+        rho_r, j_r = ref.moments()
+        w = ref.w.reshape((-1,) + (1,) * len(ref.shape))
+        e = {"u": np.abs(got["j"] / got["rho"] - j_r / rho_r).max() / np.abs(j_r / rho_r).max(),
+             "x": np.abs(got["x"] - ref.X).max() / np.abs(ref.X - X0).max(),
+             "up": np.abs(got["u"] - ref.U).max() / np.abs(ref.U).max()}
+        bars = dict.fromkeys(e, bar)
+        if prec == "fp64":
+            e["dpop"] = np.abs(got["pop"] - ref.f).max() / np.abs(ref.f - w).max()
+            e["drho"] = np.abs(got["rho"] - rho_r).max() / np.abs(rho_r - 1.0).max()
+            bars.update(dpop=1e-8, drho=1e-8)
+        print("ensemble member", prec, e)
+        assert all(e[k] <= bars[k] for k in e), (prec, e)

@@ -1,11 +1,14 @@
 """Populations stored in FP16 (f - w scaled by 2^12) and BF16 (f - w) with FP32
-collision and force, particles and contacts in FP64.
+collision and force, particles and contacts in FP64, against the FP64 oracle.
 
-Bars, stated per field as a relative error against FP64:
-- velocity field, relative L2: FP16 <= 1e-3; BF16 is reported and only bounded
-  by 1e-2 (its 8-bit mantissa resolves deviations from rest to about 2^-9,
-  which accumulates to a few 1e-3);
-- particle displacement and velocity: FP16 <= 1e-3, BF16 <= 1e-2.
+Bars, stated per field as a relative error against the FP64 oracle:
+- velocity field, relative L2: FP32 <= 1e-5, FP16 <= 1e-3;
+- particle displacement and velocity: FP16 <= 1e-3.
+BF16 keeps 8 bits of mantissa, so each stored deviation f - w is resolved to
+about 2^-9 of itself and the velocity field, carried by those deviations,
+inherits an error of the same order (a few 1e-3 after 1000 steps). BF16 storage
+therefore does not meet the 1e-3 velocity bar and is not one of the qualifying
+reduced-precision forms; it is held to 1e-2 here only to catch breakage.
 """
 import numpy as np
 import pytest
@@ -63,10 +66,49 @@ def test_reduced_storage_against_fp64_oracle(precision):
     assert all(v <= BARS[precision] for v in e.values()), e
 
 
+@pytest.fixture(scope="module")
+def slice_32():
+    """32^3 D3Q19 slice with the 256^3 workload's particle density (7812 particles,
+    d = 0.6, ratio 2, top half), tau 0.55, walls, gravity 1e-5, 4-point kernel:
+    the FP64 oracle (OpenMP build) after 1000 steps."""
+    w = preset("c3")
+    n = (32, 32, 32)
+    npart = int(round(w.n_particles * (32 ** 3) / w.ncell))
+    X, dia, rr = sample_particles(n, npart, w.diameter, w.density_ratio, w.band, 91)
+    kw = dict(delta_width=w.delta_width, gravity=w.gravity, kn=w.kn, restitution=w.restitution,
+              x0=X, diameter=dia, density_ratio=rr)
+    ref = Oracle(19, n, w.periodic, w.tau, parallel=True, **kw)
+    ref.step(1000)
+    rho_r, j_r = ref.moments()
+    return dict(n=n, w=w, kw=kw, X0=X, rho=rho_r, j=j_r, X=ref.X.copy(), U=ref.U.copy())
+
+
+SLICE_BARS = {"fp32": 1e-5, "fp16": 1e-3, "bf16": 1e-2}
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
+def test_storage_modes_on_the_32_cubed_slice_against_the_oracle(slice_32, precision):
+    """1000 steps of the 3D workload's slice in each storage mode, in the benchmark's
+    launch configuration (cell list kept for 10 steps), against the FP64 oracle."""
+    from paper_1407_6704_gb300.pibm import Pibm
+
+    c = slice_32
+    w = c["w"]
+    with Pibm("d3q19", c["n"], w.periodic, w.tau, precision=precision, rebin_every=10,
+              **c["kw"]) as sim:
+        sim.step(1000)
+        got = sim.read("rho", "j", "x", "u")
+        assert sim.status() == 0
+    e = _errors(got, c["rho"], c["j"], c["X"], c["U"], c["X0"])
+    print("32^3 slice", precision, e)
+    assert all(v <= SLICE_BARS[precision] for v in e.values()), e
+
+
 def test_fp16_on_the_64_cubed_slice_of_the_3d_workload():
     """64^3 D3Q19 slice with the 3D workload's particle density (62,500 particles,
-    d = 0.6, ratio 2, top half), 1000 steps: FP16 storage against the FP64 path
-    (which matches the oracle to 1e-12 on full-size steps)."""
+    d = 0.6, ratio 2, top half), 1000 steps: FP16 storage against the library's
+    FP64 path at this size (a consistency check; the brute-force oracle is too slow
+    for 62,500 particles, and the oracle comparison is the 32^3 test above)."""
     from paper_1407_6704_gb300.inputs import workload_particles
     from paper_1407_6704_gb300.pibm import Pibm
 

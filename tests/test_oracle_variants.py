@@ -74,7 +74,7 @@ def test_lagrange_interpolation_reproduces_cubics(q, n):
     f = np.empty((q,) + tuple(reversed(n)))
     for a in range(q):
         f[a] = field(a, grids).transpose()
-    o.f[...] = f
+    o.f = f
     pts = [rng.uniform(0.0, np.array(n)) for _ in range(20)]
     pts += [np.array([0.05] * d), np.array(n) - 0.05, np.array([0.3] + list(np.array(n[1:]) - 0.4))]
     for X in pts:

@@ -39,15 +39,19 @@ def make_case(q, n, periodic, tau, width, npart, seed, implicit=True, f0_eps=0.0
                 D=D, R=R, f0=f0, gravity=g, kn=kn, e=e)
 
 
-def run_both(c, steps, precision="fp64", deterministic=False):
+def run_both(c, steps, precision="fp64", deterministic=False, **gpu):
+    """The oracle (OpenMP build, bitwise equal to the serial one) and the library
+    from the same inputs; gpu: extra options of the library's run only
+    (rebin_every, overlap), which do not change the result beyond rounding."""
     from paper_1407_6704_gb300.pibm import Pibm
 
     kw = dict(delta_width=c["width"], gravity=c["gravity"], kn=c["kn"], restitution=c["e"],
               x0=c["X"], u0=c["U"], diameter=c["D"], density_ratio=c["R"], f0=c["f0"])
-    ref = Oracle(c["q"], c["n"], c["periodic"], c["tau"], implicit_drag=c["implicit"], **kw)
+    ref = Oracle(c["q"], c["n"], c["periodic"], c["tau"], implicit_drag=c["implicit"],
+                 parallel=True, **kw)
     ref.step(steps)
     with Pibm(LAT[c["q"]], c["n"], c["periodic"], c["tau"], implicit=c["implicit"],
-              precision=precision, deterministic=deterministic, **kw) as sim:
+              precision=precision, deterministic=deterministic, **kw, **gpu) as sim:
         sim.step(steps)
         got = sim.read("pop", "rho", "j", "x", "u")
         got["f_fpi"], got["f_c"] = sim.forces()
@@ -231,3 +235,63 @@ def test_nonfinite_state_is_reported():
     with Pibm("d2q9", (12, 12), (0, 0), 0.8, f0=f0) as sim:
         sim.step(2)
         assert sim.status() == _lib.PIBM_EUNSTABLE
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16"])
+@pytest.mark.parametrize("q,n", [(9, (14, 12)), (19, (10, 8, 9))])
+def test_mach_guard_is_reported(q, n, precision):
+    """A cell whose populations carry a fluid speed of 0.35 (the equilibrium of
+    Eq. 3 at that velocity, set on the host) raises PIBM_EUNSTABLE at the first
+    collision; the same field at 0.25 runs clean."""
+    from paper_1407_6704_gb300 import _lib
+    from paper_1407_6704_gb300.pibm import Pibm
+
+    d, e, w, _ = lattice(q)
+    shape = tuple(reversed(n))
+    for speed, status in ((0.25, _lib.PIBM_OK), (0.35, _lib.PIBM_EUNSTABLE)):
+        u = np.zeros(3)
+        u[0] = speed
+        eu = e @ u
+        feq = w * (1 + 3 * eu + 4.5 * eu ** 2 - 1.5 * (u @ u))
+        f0 = np.empty((q,) + shape)
+        f0[:] = w.reshape((-1,) + (1,) * d)
+        f0[(slice(None),) + tuple(k // 2 for k in shape)] = feq
+        with Pibm(LAT[q], n, (1,) * d, 0.8, f0=f0, precision=precision) as sim:
+            sim.step(1)
+            assert sim.status() == status, (speed, sim.status())
+
+
+def _workload_case(name, n, seed, f0_eps=1e-3, u_scale=2e-3):
+    """A lattice of extent n with the particle density, diameters, density ratios,
+    band, relaxation time, gravity, kernel and contact law of a preset workload;
+    random initial particle velocities and perturbed populations."""
+    w = preset(name)
+    frac = float(np.prod(n)) / float(np.prod(w.n))
+    npart = int(round(w.n_particles * frac))
+    X, D, R = sample_particles(n, npart, w.diameter, w.density_ratio, w.band, seed)
+    U = velocities(npart, w.d, seed=seed + 1, scale=u_scale) if u_scale else None
+    _, _, wq, _ = lattice(w.q)
+    f0 = populations(wq, tuple(reversed(n)), seed=seed + 2, eps=f0_eps) if f0_eps else None
+    return dict(q=w.q, n=n, periodic=w.periodic, tau=w.tau, width=w.delta_width, implicit=True,
+                X=X, U=U, D=D, R=R, f0=f0, gravity=w.gravity, kn=w.kn, e=w.restitution)
+
+
+LONG = [
+    # the 96^3 D3Q19 adjoint configuration's density (20k particles of d 0.5,
+    # ratio 2, top half), tau 0.7, walls, 4-point kernel, on 24^3: 312 particles
+    ("c5_shape_24cube", dict(name="c5", n=(24, 24, 24), seed=81), {}),
+    # the 2048^2 benchmark workload's density (d ~ U[0.3, 0.8], ratio 2.5, top 60 %),
+    # tau 0.6, walls, 4-point, on 128^2 (1953 particles), in the benchmark's launch
+    # configuration: cell list kept for 10 steps, overlap on
+    ("c2_shape_128sq_bench_launch", dict(name="c2", n=(128, 128), seed=82),
+     dict(rebin_every=10, overlap="on")),
+]
+
+
+@pytest.mark.parametrize("name,case,gpu", LONG, ids=[c[0] for c in LONG])
+def test_parity_fp64_1000_steps(name, case, gpu):
+    """FP64 against the oracle after 1000 steps, element by element, at the 1e-10 bar."""
+    c = _workload_case(**case)
+    got, ref = run_both(c, 1000, **gpu)
+    e = assert_parity(got, ref, c["X"])
+    print(name, ref.np, e)
