@@ -599,23 +599,116 @@ def cpu_sample(w, side=256):
     return (side, side), X, dia, rr
 
 
-def cpu_baseline(args, w, budget_s=15.0):
-    from oracle.oracle import Oracle
-    n, X, dia, rr = cpu_sample(w)
-    o = Oracle(w.q, n, w.periodic, w.tau, delta_width=w.delta_width, gravity=w.gravity,
-               kn=w.kn, restitution=w.restitution, x0=X, diameter=dia, density_ratio=rr)
-    o.step(1)
+def cpu_info():
+    """(logical cores, CPU model) of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for line in fh:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return os.cpu_count() or 1, model or "unknown"
+
+
+def _timed_oracle(o, budget_s, max_steps=None):
+    """Steps of the oracle o for about budget_s seconds: (steps, seconds)."""
     t0 = time.perf_counter()
     steps = 0
-    while time.perf_counter() - t0 < budget_s:
+    while time.perf_counter() - t0 < budget_s and (max_steps is None or steps < max_steps):
         o.step(1)
         steps += 1
-    dt = time.perf_counter() - t0
-    cells = n[0] * n[1]
-    return {"value": cells * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{n[0]}x{n[1]} patch of the workload with the same particle density "
-                      f"({len(X)} particles), {steps} steps, {dt:.1f} s, single thread",
+    return steps, time.perf_counter() - t0
+
+
+def cpu_baseline(args, w, budget_s=8.0):
+    """The oracle (test infrastructure, FP64, brute-force contacts) timed on this
+    host's cores on bounded samples of the workloads: the serial build and the
+    OpenMP build (cell loops and per-particle updates on every core, the spreading
+    serial; bitwise equal results). The headline figure is the OpenMP build on a
+    256^2 patch of the benchmark workload with its particle density. The full-size
+    lattices of the 2048^2 and 256^3 workloads are timed for the fluid step alone:
+    with particles, the brute-force contact search alone would test N^2 pairs per
+    step (2.5e11 and 1.6e13); their particle phase is projected from the per-pair
+    cost measured here."""
+    from oracle.oracle import Oracle
+    from paper_1407_6704_gb300.inputs import preset, sample_particles
+
+    nproc, model = cpu_info()
+    legs = {}
+    n, X, dia, rr = cpu_sample(w)
+    kw = dict(delta_width=w.delta_width, gravity=w.gravity, kn=w.kn, restitution=w.restitution,
+              x0=X, diameter=dia, density_ratio=rr)
+    for par in (False, True):
+        o = Oracle(w.q, n, w.periodic, w.tau, parallel=par, **kw)
+        o.step(1)
+        steps, dt = _timed_oracle(o, budget_s)
+        legs["patch_" + ("openmp" if par else "serial")] = {
+            "threads": nproc if par else 1, "steps": steps, "seconds": dt,
+            "mlups": n[0] * n[1] * steps / dt / 1e6,
             "particle_updates_per_s": len(X) * steps / dt}
+    # the per-pair cost of the brute-force contact search: the patch with and
+    # without its particles (OpenMP)
+    o = Oracle(w.q, n, w.periodic, w.tau, parallel=True, delta_width=w.delta_width)
+    o.step(1)
+    steps, dt_fluid = _timed_oracle(o, 2.0)
+    sec_fluid = dt_fluid / steps
+    sec_with = 1.0 / (legs["patch_openmp"]["mlups"] * 1e6 / (n[0] * n[1]))
+    pair_s = max(sec_with - sec_fluid, 0.0) / float(len(X)) ** 2
+    # the 128^2 workload in full: 200 particles, 2-point kernel, 1000 steps
+    c1 = preset("c1")
+    X1, d1, r1 = sample_particles(c1.n, c1.n_particles, c1.diameter, c1.density_ratio, c1.band,
+                                  c1.seed)
+    o = Oracle(c1.q, c1.n, c1.periodic, c1.tau, parallel=True, delta_width=c1.delta_width,
+               gravity=c1.gravity, kn=c1.kn, restitution=c1.restitution, x0=X1, diameter=d1,
+               density_ratio=r1)
+    t0 = time.perf_counter()
+    o.step(c1.steps)
+    dt = time.perf_counter() - t0
+    legs["c1_full_1000_steps"] = {"threads": nproc, "seconds": dt,
+                                  "mlups": c1.ncell * c1.steps / dt / 1e6}
+    # full-size lattices, fluid step alone, and the projected particle phase
+    for name in ("c2", "c3"):
+        wf = preset(name)
+        o = Oracle(wf.q, wf.n, wf.periodic, wf.tau, parallel=True, delta_width=wf.delta_width)
+        steps, dt = _timed_oracle(o, 1.0, max_steps=2)
+        fl = dt / steps
+        proj = fl + pair_s * float(wf.n_particles) ** 2
+        legs[name + "_full_size"] = {
+            "threads": nproc, "cells": wf.ncell, "particles": wf.n_particles,
+            "fluid_step_seconds": fl, "fluid_mlups": wf.ncell / fl / 1e6,
+            "projected_step_seconds_with_particles": proj,
+            "projected_mlups_with_particles": wf.ncell / proj / 1e6}
+        del o
+    # the 64^3 slice of the 256^3 workload (62,500 particles), OpenMP, 2 steps
+    ws = preset("c3s")
+    Xs, ds, rs = sample_particles(ws.n, ws.n_particles, ws.diameter, ws.density_ratio, ws.band,
+                                  ws.seed)
+    o = Oracle(ws.q, ws.n, ws.periodic, ws.tau, parallel=True, delta_width=ws.delta_width,
+               gravity=ws.gravity, kn=ws.kn, restitution=ws.restitution, x0=Xs, diameter=ds,
+               density_ratio=rs)
+    steps, dt = _timed_oracle(o, 1.0, max_steps=2)
+    legs["c3_slice_64cubed"] = {"threads": nproc, "steps": steps, "seconds": dt,
+                                "mlups": ws.ncell * steps / dt / 1e6,
+                                "particle_updates_per_s": ws.n_particles * steps / dt}
+    head = legs["patch_openmp"]
+    return {"value": head["mlups"], "unit": "MLUPS", "cores": nproc, "kind": "oracle",
+            "sample": f"{n[0]}x{n[1]} patch of the workload with the same particle density "
+                      f"({len(X)} particles), OpenMP build on all {nproc} cores, "
+                      f"{head['steps']} steps in {head['seconds']:.1f} s",
+            "particle_updates_per_s": head["particle_updates_per_s"],
+            "nproc": nproc, "cpu_model": model, "pair_test_seconds": pair_s, "legs": legs}
 
 
 def run_reference(args, rank, world):
@@ -629,8 +722,10 @@ def run_reference(args, rank, world):
     total = args.steps + max(args.warmup, 0)
     side = 256 if total <= 200 else (128 if total <= 4000 else 64)
     n, X, dia, rr = cpu_sample(w, side)
+    nproc, model = cpu_info()
     o = Oracle(w.q, n, w.periodic, w.tau, delta_width=w.delta_width, gravity=w.gravity,
-               kn=w.kn, restitution=w.restitution, x0=X, diameter=dia, density_ratio=rr)
+               kn=w.kn, restitution=w.restitution, x0=X, diameter=dia, density_ratio=rr,
+               parallel=True)
     o.step(max(args.warmup, 0))
     t0 = time.perf_counter()
     o.step(args.steps)
@@ -643,9 +738,11 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD_DESC, "lattice": "D2Q9",
                                             "n": list(n), "particles": len(X)},
-            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": nproc, "kind": "oracle",
+                             "cpu_model": model,
                              "sample": f"{n[0]}x{n[1]} patch with the workload's particle "
-                                       f"density ({len(X)} particles), single thread"},
+                                       f"density ({len(X)} particles), OpenMP build of the "
+                                       f"oracle on all {nproc} cores"},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
