@@ -579,25 +579,27 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
   }
 
   if (np > 0) {
-    // AoS -> SoA on the host, then upload
-    std::vector<double> soa((size_t)d * np);
-    for (int k = 0; k < d; ++k)
-      for (long long p = 0; p < np; ++p) soa[(size_t)k * np + p] = cfg->x0[p * d + k];
-    if (cudaMemcpyAsync(P.X[0], soa.data(), sizeof(double) * d * np, cudaMemcpyHostToDevice,
-                        st) != cudaSuccess)
+    // The AoS arrays go up as they are, into the second particle buffers (free
+    // before the first step), and are transposed to SoA on the device; one
+    // synchronisation at the end covers every copy.
+    const size_t vb = sizeof(double) * d * np;
+    if (cudaMemcpyAsync(P.X[1], cfg->x0, vb, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        launch_aos_to_soa(np, d, P.X[1], P.X[0], st) != cudaSuccess)
       return fail(PIBM_ECUDA);
-    if (cudaStreamSynchronize(st) != cudaSuccess) return fail(PIBM_ECUDA);
-    for (int k = 0; k < d; ++k)
-      for (long long p = 0; p < np; ++p)
-        soa[(size_t)k * np + p] = cfg->u0 ? cfg->u0[p * d + k] : 0.0;
-    if (cudaMemcpyAsync(P.U[0], soa.data(), sizeof(double) * d * np, cudaMemcpyHostToDevice,
-                        st) != cudaSuccess ||
-        cudaMemcpyAsync(P.rad[0], cfg->diameter, sizeof(double) * np, cudaMemcpyHostToDevice,
+    if (cfg->u0) {
+      if (cudaMemcpyAsync(P.U[1], cfg->u0, vb, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+          launch_aos_to_soa(np, d, P.U[1], P.U[0], st) != cudaSuccess)
+        return fail(PIBM_ECUDA);
+    } else if (cudaMemsetAsync(P.U[0], 0, vb, st) != cudaSuccess) {
+      return fail(PIBM_ECUDA);
+    }
+    if (cudaMemcpyAsync(P.rad[0], cfg->diameter, sizeof(double) * np, cudaMemcpyHostToDevice,
                         st) != cudaSuccess ||
         cudaMemcpyAsync(P.buoy[0], cfg->density_ratio, sizeof(double) * np,
                         cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemsetAsync(P.g, 0, sizeof(double) * d * np, st) != cudaSuccess ||
-        cudaMemsetAsync(P.Fc, 0, sizeof(double) * d * np, st) != cudaSuccess ||
+        cudaMemsetAsync(P.g, 0, vb, st) != cudaSuccess ||
+        cudaMemsetAsync(P.Fc, 0, vb, st) != cudaSuccess ||
+        cudaMemsetAsync(P.Fcf, 0, sizeof(float) * d * np, st) != cudaSuccess ||
         launch_particle_init(s, st) != cudaSuccess)
       return fail(PIBM_ECUDA);
   }
@@ -730,8 +732,16 @@ int pibm_read_fields(pibm_t* h, unsigned mask, void* const* dst, int on_device) 
     double* o = (double*)dst[f == 0 ? 3 : 4];
     if (on_device) {
       CK(launch_interleave(s, src, o, st));
+    } else if ((size_t)2 * d * np * sizeof(double) <=
+               align_up((size_t)s.geo.q * s.geo.pitch * pop_bytes(s.precision))) {
+      // storage order -> user order on the device, in the partner population
+      // buffer (free between steps), then one copy into the caller's array
+      double* aos = stage + (size_t)f * d * np;
+      CK(launch_interleave(s, src, aos, st));
+      CK(cudaMemcpyAsync(o, aos, sizeof(double) * d * np, cudaMemcpyDeviceToHost, st));
     } else {
-      // storage order -> user order on the host
+      // a lattice too small to stage the particles: storage order -> user order
+      // on the host
       std::vector<double> soa((size_t)d * np);
       std::vector<unsigned> pid((size_t)np);
       CK(cudaMemcpyAsync(soa.data(), src, sizeof(double) * d * np, cudaMemcpyDeviceToHost, st));

@@ -1476,6 +1476,14 @@ __global__ void k_forces(long long np, int d, const double* __restrict__ Ap,
   }
 }
 
+// aos[p][k] (user order) -> soa[k][p] (storage order at creation: the same).
+__global__ void k_aos_to_soa(long long np, int d, const double* __restrict__ aos,
+                             double* __restrict__ soa) {
+  long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  for (int k = 0; k < d; ++k) soa[k * np + p] = aos[p * d + k];
+}
+
 __global__ void k_interleave(long long np, int d, const double* __restrict__ soa,
                              const unsigned* __restrict__ pid, double* __restrict__ aos,
                              unsigned* __restrict__ err) {
@@ -1771,6 +1779,13 @@ cudaError_t launch_particle_forces(const State& s, double* f_fpi, double* f_c, c
   const Particles& P = s.p;
   k_forces<<<blocks_for(P.np, 256), 256, 0, st>>>(P.np, s.geo.d, P.Ap[s.cur], P.g, P.Fc,
                                                   P.pid[s.cur], f_fpi, f_c, s.err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_aos_to_soa(long long np, int d, const double* aos, double* soa,
+                              cudaStream_t st) {
+  if (np == 0) return cudaSuccess;
+  k_aos_to_soa<<<blocks_for(np, 256), 256, 0, st>>>(np, d, aos, soa);
   return cudaGetLastError();
 }
 

@@ -496,6 +496,9 @@ cudaError_t launch_couple(const State& s, cudaStream_t st, int* nkernels,
 cudaError_t launch_particle_forces(const State& s, double* f_fpi, double* f_c, cudaStream_t st);
 // X or U of the current state (SoA by storage position) into aos[user index][d].
 cudaError_t launch_interleave(const State& s, const double* soa, double* aos, cudaStream_t st);
+// aos [np][d] -> soa [d][np], both device memory.
+cudaError_t launch_aos_to_soa(long long np, int d, const double* aos, double* soa,
+                              cudaStream_t st);
 // Derive radius, mass, A_p and buoyancy factor in buffer 0 and number the
 // particles in user order; expects the diameter in p.rad[0] and the density ratio
 // in p.buoy[0] on entry.

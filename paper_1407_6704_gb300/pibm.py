@@ -146,17 +146,27 @@ class Pibm:
                                       fc.ctypes.data_as(ctypes.c_void_p), 0), "pibm_forces")
         return ffpi, fc
 
-    def read(self, *names):
-        """Host copies of the requested fields: 'rho', 'j', 'pop', 'x', 'u'."""
+    def read(self, *names, out=None):
+        """Host copies of the requested fields: 'rho', 'j', 'pop', 'x', 'u'. out: an
+        optional dict of preallocated C-contiguous FP64 arrays (for example in pinned
+        memory) to fill instead of new ones."""
         bits = {"rho": (0, FIELD_RHO, (self.ncell,)), "j": (1, FIELD_J, (self.d, self.ncell)),
                 "pop": (2, FIELD_POP, (self.q, self.ncell)), "x": (3, FIELD_X, (self.np, self.d)),
                 "u": (4, FIELD_U, (self.np, self.d))}
+        given = out or {}
         out = {}
         dst = (ctypes.c_void_p * _lib.NFIELDS)()
         mask = 0
         for nm in names:
             k, bit, shp = bits[nm]
-            arr = np.zeros(shp)
+            if nm in given:
+                arr = given[nm]
+                if (arr.dtype != np.float64 or not arr.flags.c_contiguous
+                        or arr.size != int(np.prod(shp))):
+                    raise ValueError(f"out[{nm!r}] must be C-contiguous FP64 of {shp}")
+                arr = arr.reshape(shp)
+            else:
+                arr = np.zeros(shp)
             out[nm] = arr
             dst[k] = arr.ctypes.data_as(ctypes.c_void_p).value if arr.size else 1
             mask |= bit if arr.size else 0
