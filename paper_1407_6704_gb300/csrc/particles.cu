@@ -1266,6 +1266,261 @@ __global__ void __launch_bounds__(256, sizeof(typename St::R) == 4 ? (Lattice<Q>
   }
 }
 
+// 3D coupling by tiles (32- and 16-bit storage, delta interpolation, atomic
+// spreading). The scattered moment gathers and force atomics of k_couple (W^3 of
+// each per particle) are bound by L1 sector requests. Here one CTA takes up to 256
+// particles of one cell-list tile (chunk `blockIdx.x % CHUNKS` of tile
+// `blockIdx.x / CHUNKS`; the particles of a tile are contiguous in the sorted
+// order) and works in a shared-memory window of the lattice that covers every
+// stencil node of its particles (the box of their unwrapped tap indices):
+//   1. the window is filled with the moment field by coalesced loads (periodic
+//      axes wrap; nodes beyond a wall read zero and carry weight zero);
+//   2. each particle interpolates from the window in the order of
+//      gather_moments, so rho_l and j_l equal the direct path's bit for bit, and
+//      advances as in k_couple;
+//   3. the window is cleared and each particle adds A_p g w into it (the weights
+//      of spread_amp), in fixed point: shared-memory atomic adds of 32-bit
+//      integers are native, those of floats are not. Each component k has a
+//      power-of-two scale chosen per CTA so that no sum can overflow: 2^30 over
+//      the sum, over the CTA's particles, of |A_p g_k| times the particle's
+//      largest weight product, which bounds every node's sum of that component.
+//      A contribution is then resolved to about 1e-9 of that bound (for the
+//      cosine kernel away from walls the largest weight product is about 1/8, so
+//      the bound is some tens of contributions), and the sums are exact
+//      (independent of their order);
+//   4. every window node with a non-zero force is added to the force field by
+//      one 16-byte atomic, converted back to FP32.
+// The last chunk of a tile takes every remaining particle; beyond 256 of them,
+// or if the box exceeds the window, the CTA falls back to the direct path.
+constexpr int TILE_CHUNKS = 2;
+
+template <int W>
+struct CoupleWindow {
+  using TD = TileDims<3>;
+  // the taps of a particle lie within W + 1 cells of its tile along each axis
+  static constexpr int VMAX = (TD::TX + W + 1) * (TD::TY + W + 1) * (TD::TZ + W + 1);
+};
+
+template <int Q, int W, class St, typename FT>
+__global__ void __launch_bounds__(256, 3) k_couple_tiles(CoupleArgs A) {
+  using R = typename St::R;
+  using Win = CoupleWindow<W>;
+  constexpr int D = 3;
+  static_assert(Lattice<Q>::D == 3 && sizeof(R) == 4 && sizeof(FT) == 4, "3D, FP32 arithmetic");
+  __shared__ float4 win[Win::VMAX];
+  __shared__ int box[6];
+  __shared__ float amp_bound[8][3];  // per warp and component: sum of |A_p g_k| w_max
+  const Geometry& g = A.g;
+  const long long np = A.np;
+  const long long tile = blockIdx.x / TILE_CHUNKS;
+  const int chunk = blockIdx.x % TILE_CHUNKS;
+  const unsigned t_lo = A.start[tile * A.bm.tc], t_hi = A.start[(tile + 1) * A.bm.tc];
+  const unsigned lo = t_lo + 256u * chunk;
+  if (lo >= t_hi) return;  // uniform across the CTA
+  const unsigned hi = chunk == TILE_CHUNKS - 1 ? t_hi : min(t_hi, lo + 256u);
+  if (hi > (unsigned)np || t_lo > t_hi) {
+    if (threadIdx.x == 0) atomicOr(A.err, ERR_INDEX);
+    return;
+  }
+  if (threadIdx.x < 3) {
+    box[threadIdx.x] = INT_MAX;
+    box[3 + threadIdx.x] = INT_MIN;
+  }
+  __syncthreads();
+  const bool windowed0 = hi - lo <= 256u;
+  // --- each thread's particle: record and taps (FP32 from the record) ---
+  const unsigned sl = lo + threadIdx.x;
+  bool act = windowed0 && sl < hi;
+  int4 mc = make_int4(0, 0, 0, 0);
+  float4 mf = make_float4(0.f, 0.f, 0.f, 0.f);
+  unsigned p = 0;
+  double X[3] = {0.0, 0.0, 0.0};
+  Taps<W, R> tx, ty, tz;
+  if (act) {
+    mc = A.cs[sl];
+    mf = A.xs[sl];
+    p = (unsigned)mc.w;
+    if (p >= (unsigned)np) {
+      atomicOr(A.err, ERR_INDEX);
+      act = false;
+    }
+  }
+  if (act) {
+    particle_taps<D, W, false, R>(g, mc, mf, X, tx, ty, tz);
+    atomicMin(&box[0], tx.first);
+    atomicMin(&box[1], ty.first);
+    atomicMin(&box[2], tz.first);
+    atomicMax(&box[3], tx.first + W - 1);
+    atomicMax(&box[4], ty.first + W - 1);
+    atomicMax(&box[5], tz.first + W - 1);
+  }
+  __syncthreads();
+  const int bx = box[0], by = box[1], bz = box[2];
+  // extents in 64 bits: a box that no particle set stays empty (max < min)
+  const long long wxl = (long long)box[3] - bx + 1, wyl = (long long)box[4] - by + 1,
+                  wzl = (long long)box[5] - bz + 1;
+  const bool windowed = windowed0 && wxl > 0 && wyl > 0 && wzl > 0 &&
+                        wxl * wyl * wzl <= Win::VMAX;
+  const int wx = (int)wxl, wy = (int)wyl, wz = (int)wzl;
+  if (!windowed) {
+    // the direct path, one particle at a time per thread
+    for (unsigned s2 = lo + threadIdx.x; s2 < hi; s2 += blockDim.x) {
+      const int4 c2 = A.cs[s2];
+      const float4 f2 = A.xs[s2];
+      const unsigned p2 = (unsigned)c2.w;
+      if (p2 >= (unsigned)np) {
+        atomicOr(A.err, ERR_INDEX);
+        continue;
+      }
+      double X2[3], U2[3];
+      R Fc2[3];
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        X2[k] = A.X[k * np + p2];
+        U2[k] = A.U[k * np + p2];
+        Fc2[k] = A.Fcf[k * np + s2];
+      }
+      Taps<W, R> ax, ay, az;
+      particle_taps<D, W, false, R>(g, c2, f2, X2, ax, ay, az);
+      R rs2, js2[3];
+      gather_moments<D, W, R>(A, ax, ay, az, rs2, js2);
+      FT amp2[3] = {FT(0), FT(0), FT(0)};
+      advance_particle<D, St, FT>(A, s2, p2, c2, f2, X2, U2, Fc2, rs2, js2, amp2);
+      spread_amp<D, W, R, FT>(A, ax, ay, az, amp2);
+    }
+    return;
+  }
+  const int V = wx * wy * wz;
+  // --- 1. the moment field over the window ---
+  {
+    const float4* mom = (const float4*)A.mom;
+    for (int v = threadIdx.x; v < V; v += blockDim.x) {
+      int cx = bx + v % wx, cy = by + (v / wx) % wy, cz = bz + v / (wx * wy);
+      const bool in = lattice_coord(cx, g.n[0], g.periodic[0]) &&
+                      lattice_coord(cy, g.n[1], g.periodic[1]) &&
+                      lattice_coord(cz, g.n[2], g.periodic[2]);
+      win[v] = in ? __ldg(mom + cx + (long long)g.n[0] * (cy + (long long)g.n[1] * cz))
+                  : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  __syncthreads();
+  // --- 2. interpolation (Eq. 4) and the particle update (Eq. 13) ---
+  FT amp[3] = {FT(0), FT(0), FT(0)};
+  if (act) {
+    double U[3] = {0.0, 0.0, 0.0};
+    R Fc[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      X[k] = A.X[k * np + p];
+      U[k] = A.U[k * np + p];
+      Fc[k] = A.Fcf[k * np + sl];
+    }
+    R rs = R(0), js[3] = {R(0), R(0), R(0)};
+#pragma unroll 1
+    for (int iz = 0; iz < W; ++iz) {
+      const R wzz = pick(tz.w, iz);
+      if (wzz == R(0)) continue;
+      const int oz = (tz.first + iz - bz) * wy;
+#pragma unroll
+      for (int iy = 0; iy < W; ++iy) {
+        const R wyz = ty.w[iy] * wzz;
+        const int row = (oz + ty.first + iy - by) * wx + tx.first - bx;
+#pragma unroll
+        for (int ix = 0; ix < W; ++ix) {
+          const float4 m = win[row + ix];
+          const R wt = tx.w[ix] * wyz;
+          rs += wt * m.x;
+          js[0] += wt * m.y;
+          js[1] += wt * m.z;
+          js[2] += wt * m.w;
+        }
+      }
+    }
+    advance_particle<D, St, FT>(A, sl, p, mc, mf, X, U, Fc, rs, js, amp);
+  }
+  // the fixed-point scales: per component, a bound on every node's |sum|
+  {
+    float wm = 0.f;
+    if (act) {
+      float mx = 0.f, my = 0.f, mz = 0.f;
+#pragma unroll
+      for (int i = 0; i < W; ++i) {
+        mx = fmaxf(mx, tx.w[i]);
+        my = fmaxf(my, ty.w[i]);
+        mz = fmaxf(mz, tz.w[i]);
+      }
+      wm = mx * my * mz;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float b = fabsf(amp[k]) * wm;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+      if ((threadIdx.x & 31) == 0) amp_bound[threadIdx.x >> 5][k] = b;
+    }
+  }
+  __syncthreads();  // every particle has read the window
+  // per component: the largest power of two with bound * scale <= 2^30 (1 if the
+  // bound is zero or not finite: the step is then flagged unstable anyway); the
+  // bound is rounded up a little so that FP32 rounding of the sums cannot
+  // undercut it
+  float scale[3], inv_scale[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float bound = 0.f;
+#pragma unroll
+    for (int w8 = 0; w8 < 8; ++w8) bound += amp_bound[w8][k];
+    bound *= 1.0001f;
+    scale[k] = 1.f;
+    if (bound > 0.f && bound < 3.0e38f)
+      scale[k] = exp2f(fminf(floorf(log2f(1073741824.f / bound)), 126.f));
+    inv_scale[k] = 1.f / scale[k];  // exact: a power of two
+  }
+  // --- 3. A_p g w into the window (Eq. 9) ---
+  int4* wi = reinterpret_cast<int4*>(win);
+  for (int v = threadIdx.x; v < V; v += blockDim.x) wi[v] = make_int4(0, 0, 0, 0);
+  __syncthreads();
+  if (act) {
+#pragma unroll 1
+    for (int iz = 0; iz < W; ++iz) {
+      const FT wzz = (FT)pick(tz.w, iz);
+      if (wzz == FT(0)) continue;
+      const int oz = (tz.first + iz - bz) * wy;
+#pragma unroll
+      for (int iy = 0; iy < W; ++iy) {
+        const FT wyz = (FT)ty.w[iy] * wzz;
+        const int row = (oz + ty.first + iy - by) * wx + tx.first - bx;
+#pragma unroll
+        for (int ix = 0; ix < W; ++ix) {
+          const FT wt = (FT)tx.w[ix] * wyz;
+          if (wt == FT(0)) continue;
+          int* c = reinterpret_cast<int*>(wi + row + ix);
+          atomicAdd(c + 0, __float2int_rn(amp[0] * wt * scale[0]));
+          atomicAdd(c + 1, __float2int_rn(amp[1] * wt * scale[1]));
+          atomicAdd(c + 2, __float2int_rn(amp[2] * wt * scale[2]));
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // --- 4. the window's force into the force field ---
+  float4* F = (float4*)A.F;
+  for (int v = threadIdx.x; v < V; v += blockDim.x) {
+    const int4 q = wi[v];
+    if (q.x == 0 && q.y == 0 && q.z == 0) continue;
+    const float4 f = make_float4((float)q.x * inv_scale[0], (float)q.y * inv_scale[1],
+                                 (float)q.z * inv_scale[2], 0.f);
+    int cx = bx + v % wx, cy = by + (v / wx) % wy, cz = bz + v / (wx * wy);
+    if (!(lattice_coord(cx, g.n[0], g.periodic[0]) && lattice_coord(cy, g.n[1], g.periodic[1]) &&
+          lattice_coord(cz, g.n[2], g.periodic[2]))) {
+      atomicOr(A.err, ERR_INDEX);  // only zero weights fall beyond a wall
+      continue;
+    }
+    atomicAdd(F + cx + (long long)g.n[0] * (cy + (long long)g.n[1] * cz),
+              make_float4(f.x, f.y, f.z, 0.f));
+  }
+}
+
 // DEM sub-cycling, step start: interpolate rho_l, j_l once (Eq. 4 / Eq. 5) and
 // store them by slot, copy the step-n state to the slot-ordered buffers Xn, Un
 // (the sub-step state), clear the accumulated force density and contact force,
@@ -1673,7 +1928,16 @@ cudaError_t couple_t(const State& s, cudaStream_t st, int* nk, cudaEvent_t befor
   }
   int n = 1;
   if (s.phy.substeps <= 1) {
-    if (s.phy.lagrange) {
+    bool tiled = false;
+    if constexpr (D == 3 && sizeof(R) == 4) {
+      // 3D, FP32 arithmetic, delta interpolation, atomic spreading: by tiles
+      if (!s.phy.lagrange && A.spread) {
+        k_couple_tiles<Q, W, St, FT><<<(unsigned)(P.ntiles * TILE_CHUNKS), 256, 0, st>>>(A);
+        tiled = true;
+      }
+    }
+    if (tiled) {
+    } else if (s.phy.lagrange) {
       k_couple<Q, W, St, FT, true><<<pb, 256, 0, st>>>(A);
     } else {
       k_couple<Q, W, St, FT, false><<<pb, 256, 0, st>>>(A);
