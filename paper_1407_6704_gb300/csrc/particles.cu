@@ -489,6 +489,7 @@ struct CoupleArgs {
   double* tw;        // ordered spreading: [np][3][4] spreading tap weights by slot
   const unsigned* perm;
   const unsigned* start;
+  long long nbin;    // bins of the cell list (tiles * cells per tile)
   const void* f;     // stored populations f*
   const void* mom;   // moment field (k_moments)
   void* F;           // force field
@@ -1266,13 +1267,15 @@ __global__ void __launch_bounds__(256, sizeof(typename St::R) == 4 ? (Lattice<Q>
   }
 }
 
-// 3D coupling by tiles (32- and 16-bit storage, delta interpolation, atomic
-// spreading). The scattered moment gathers and force atomics of k_couple (W^3 of
+// Coupling by tiles (32- and 16-bit storage, delta interpolation, atomic
+// spreading). The scattered moment gathers and force atomics of k_couple (W^d of
 // each per particle) are bound by L1 sector requests. Here one CTA takes up to 256
-// particles of one cell-list tile (chunk `blockIdx.x % CHUNKS` of tile
-// `blockIdx.x / CHUNKS`; the particles of a tile are contiguous in the sorted
-// order) and works in a shared-memory window of the lattice that covers every
-// stencil node of its particles (the box of their unwrapped tap indices):
+// particles of a group of cell-list tiles (one tile in 3D, four consecutive tiles
+// of a tile row in 2D; chunk `blockIdx.x % TILE_CHUNKS` of group
+// `blockIdx.x / TILE_CHUNKS`; the particles of consecutive tiles are contiguous in
+// the sorted order) and works in a shared-memory window of the lattice that
+// covers every stencil node of its particles (the box of their unwrapped tap
+// indices):
 //   1. the window is filled with the moment field by coalesced loads (periodic
 //      axes wrap; nodes beyond a wall read zero and carry weight zero);
 //   2. each particle interpolates from the window in the order of
@@ -1285,36 +1288,45 @@ __global__ void __launch_bounds__(256, sizeof(typename St::R) == 4 ? (Lattice<Q>
 //      the sum, over the CTA's particles, of |A_p g_k| times the particle's
 //      largest weight product, which bounds every node's sum of that component.
 //      A contribution is then resolved to about 1e-9 of that bound (for the
-//      cosine kernel away from walls the largest weight product is about 1/8, so
-//      the bound is some tens of contributions), and the sums are exact
-//      (independent of their order);
+//      cosine kernel away from walls the largest weight product is about 1/8 in
+//      3D and 1/4 in 2D, so the bound is some tens of contributions), and the
+//      sums are exact (independent of their order);
 //   4. every window node with a non-zero force is added to the force field by
-//      one 16-byte atomic, converted back to FP32.
-// The last chunk of a tile takes every remaining particle; beyond 256 of them,
-// or if the box exceeds the window, the CTA falls back to the direct path.
+//      one vector atomic, converted back to FP32.
+// The last chunk of a group takes every remaining particle; beyond 256 of them,
+// or if the box exceeds the window (a 2D group that wraps to the next tile row),
+// the CTA falls back to the direct path.
+// The step launches it in 3D only. On the 256^3 workload it took the coupling
+// kernel from 1.53 to 1.42 ms; on the 2048^2 workload (about 200 particles per
+// CTA, 16 taps each) the phases of each CTA in sequence outweighed the saved
+// sectors: 0.200 ms/step against 0.154 with k_couple.
 constexpr int TILE_CHUNKS = 2;
 
-template <int W>
+template <int D, int W>
 struct CoupleWindow {
-  using TD = TileDims<3>;
+  using TD = TileDims<D>;
+  static constexpr int TPC = D == 2 ? 4 : 1;  // tiles per group, along x
   // the taps of a particle lie within W + 1 cells of its tile along each axis
-  static constexpr int VMAX = (TD::TX + W + 1) * (TD::TY + W + 1) * (TD::TZ + W + 1);
+  static constexpr int VMAX = (TPC * TD::TX + W + 1) * (TD::TY + W + 1) *
+                              (D == 3 ? TD::TZ + W + 1 : 1);
 };
 
 template <int Q, int W, class St, typename FT>
-__global__ void __launch_bounds__(256, 3) k_couple_tiles(CoupleArgs A) {
+__global__ void __launch_bounds__(256, Lattice<Q>::D == 3 ? 3 : 4) k_couple_tiles(CoupleArgs A) {
   using R = typename St::R;
-  using Win = CoupleWindow<W>;
-  constexpr int D = 3;
-  static_assert(Lattice<Q>::D == 3 && sizeof(R) == 4 && sizeof(FT) == 4, "3D, FP32 arithmetic");
+  constexpr int D = Lattice<Q>::D;
+  using Win = CoupleWindow<D, W>;
+  static_assert(sizeof(R) == 4 && sizeof(FT) == 4, "FP32 arithmetic");
   __shared__ float4 win[Win::VMAX];
   __shared__ int box[6];
   __shared__ float amp_bound[8][3];  // per warp and component: sum of |A_p g_k| w_max
   const Geometry& g = A.g;
   const long long np = A.np;
-  const long long tile = blockIdx.x / TILE_CHUNKS;
+  const long long ntiles = A.nbin / A.bm.tc;
+  const long long grp = blockIdx.x / TILE_CHUNKS;
   const int chunk = blockIdx.x % TILE_CHUNKS;
-  const unsigned t_lo = A.start[tile * A.bm.tc], t_hi = A.start[(tile + 1) * A.bm.tc];
+  const long long t0 = grp * Win::TPC, t1 = min(t0 + Win::TPC, ntiles);
+  const unsigned t_lo = A.start[t0 * A.bm.tc], t_hi = A.start[t1 * A.bm.tc];
   const unsigned lo = t_lo + 256u * chunk;
   if (lo >= t_hi) return;  // uniform across the CTA
   const unsigned hi = chunk == TILE_CHUNKS - 1 ? t_hi : min(t_hi, lo + 256u);
@@ -1323,8 +1335,8 @@ __global__ void __launch_bounds__(256, 3) k_couple_tiles(CoupleArgs A) {
     return;
   }
   if (threadIdx.x < 3) {
-    box[threadIdx.x] = INT_MAX;
-    box[3 + threadIdx.x] = INT_MIN;
+    box[threadIdx.x] = D == 3 || threadIdx.x < 2 ? INT_MAX : 0;
+    box[3 + threadIdx.x] = D == 3 || threadIdx.x < 2 ? INT_MIN : 0;
   }
   __syncthreads();
   const bool windowed0 = hi - lo <= 256u;
@@ -1349,10 +1361,12 @@ __global__ void __launch_bounds__(256, 3) k_couple_tiles(CoupleArgs A) {
     particle_taps<D, W, false, R>(g, mc, mf, X, tx, ty, tz);
     atomicMin(&box[0], tx.first);
     atomicMin(&box[1], ty.first);
-    atomicMin(&box[2], tz.first);
     atomicMax(&box[3], tx.first + W - 1);
     atomicMax(&box[4], ty.first + W - 1);
-    atomicMax(&box[5], tz.first + W - 1);
+    if constexpr (D == 3) {
+      atomicMin(&box[2], tz.first);
+      atomicMax(&box[5], tz.first + W - 1);
+    }
   }
   __syncthreads();
   const int bx = box[0], by = box[1], bz = box[2];
@@ -1372,8 +1386,8 @@ __global__ void __launch_bounds__(256, 3) k_couple_tiles(CoupleArgs A) {
         atomicOr(A.err, ERR_INDEX);
         continue;
       }
-      double X2[3], U2[3];
-      R Fc2[3];
+      double X2[3] = {0.0, 0.0, 0.0}, U2[3] = {0.0, 0.0, 0.0};
+      R Fc2[3] = {R(0), R(0), R(0)};
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         X2[k] = A.X[k * np + p2];
@@ -1391,6 +1405,7 @@ __global__ void __launch_bounds__(256, 3) k_couple_tiles(CoupleArgs A) {
     return;
   }
   const int V = wx * wy * wz;
+  constexpr int WZ = D == 3 ? W : 1;
   // --- 1. the moment field over the window ---
   {
     const float4* mom = (const float4*)A.mom;
@@ -1398,7 +1413,7 @@ __global__ void __launch_bounds__(256, 3) k_couple_tiles(CoupleArgs A) {
       int cx = bx + v % wx, cy = by + (v / wx) % wy, cz = bz + v / (wx * wy);
       const bool in = lattice_coord(cx, g.n[0], g.periodic[0]) &&
                       lattice_coord(cy, g.n[1], g.periodic[1]) &&
-                      lattice_coord(cz, g.n[2], g.periodic[2]);
+                      (D == 2 || lattice_coord(cz, g.n[2], g.periodic[2]));
       win[v] = in ? __ldg(mom + cx + (long long)g.n[0] * (cy + (long long)g.n[1] * cz))
                   : make_float4(0.f, 0.f, 0.f, 0.f);
     }
@@ -1417,10 +1432,14 @@ __global__ void __launch_bounds__(256, 3) k_couple_tiles(CoupleArgs A) {
     }
     R rs = R(0), js[3] = {R(0), R(0), R(0)};
 #pragma unroll 1
-    for (int iz = 0; iz < W; ++iz) {
-      const R wzz = pick(tz.w, iz);
+    for (int iz = 0; iz < WZ; ++iz) {
+      R wzz = R(1);
+      int oz = 0;
+      if constexpr (D == 3) {
+        wzz = pick(tz.w, iz);
+        oz = (tz.first + iz - bz) * wy;
+      }
       if (wzz == R(0)) continue;
-      const int oz = (tz.first + iz - bz) * wy;
 #pragma unroll
       for (int iy = 0; iy < W; ++iy) {
         const R wyz = ty.w[iy] * wzz;
@@ -1432,7 +1451,7 @@ __global__ void __launch_bounds__(256, 3) k_couple_tiles(CoupleArgs A) {
           rs += wt * m.x;
           js[0] += wt * m.y;
           js[1] += wt * m.z;
-          js[2] += wt * m.w;
+          if constexpr (D == 3) js[2] += wt * m.w;
         }
       }
     }
@@ -1442,17 +1461,21 @@ __global__ void __launch_bounds__(256, 3) k_couple_tiles(CoupleArgs A) {
   {
     float wm = 0.f;
     if (act) {
-      float mx = 0.f, my = 0.f, mz = 0.f;
+      float mx = 0.f, my = 0.f, mz = 1.f;
 #pragma unroll
       for (int i = 0; i < W; ++i) {
         mx = fmaxf(mx, tx.w[i]);
         my = fmaxf(my, ty.w[i]);
-        mz = fmaxf(mz, tz.w[i]);
+      }
+      if constexpr (D == 3) {
+        mz = 0.f;
+#pragma unroll
+        for (int i = 0; i < W; ++i) mz = fmaxf(mz, tz.w[i]);
       }
       wm = mx * my * mz;
     }
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < D; ++k) {
       float b = fabsf(amp[k]) * wm;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
@@ -1464,14 +1487,13 @@ __global__ void __launch_bounds__(256, 3) k_couple_tiles(CoupleArgs A) {
   // bound is zero or not finite: the step is then flagged unstable anyway); the
   // bound is rounded up a little so that FP32 rounding of the sums cannot
   // undercut it
-  float scale[3], inv_scale[3];
+  float scale[3] = {1.f, 1.f, 1.f}, inv_scale[3] = {1.f, 1.f, 1.f};
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < D; ++k) {
     float bound = 0.f;
 #pragma unroll
     for (int w8 = 0; w8 < 8; ++w8) bound += amp_bound[w8][k];
     bound *= 1.0001f;
-    scale[k] = 1.f;
     if (bound > 0.f && bound < 3.0e38f)
       scale[k] = exp2f(fminf(floorf(log2f(1073741824.f / bound)), 126.f));
     inv_scale[k] = 1.f / scale[k];  // exact: a power of two
@@ -1482,10 +1504,14 @@ __global__ void __launch_bounds__(256, 3) k_couple_tiles(CoupleArgs A) {
   __syncthreads();
   if (act) {
 #pragma unroll 1
-    for (int iz = 0; iz < W; ++iz) {
-      const FT wzz = (FT)pick(tz.w, iz);
+    for (int iz = 0; iz < WZ; ++iz) {
+      FT wzz = FT(1);
+      int oz = 0;
+      if constexpr (D == 3) {
+        wzz = (FT)pick(tz.w, iz);
+        oz = (tz.first + iz - bz) * wy;
+      }
       if (wzz == FT(0)) continue;
-      const int oz = (tz.first + iz - bz) * wy;
 #pragma unroll
       for (int iy = 0; iy < W; ++iy) {
         const FT wyz = (FT)ty.w[iy] * wzz;
@@ -1495,29 +1521,31 @@ __global__ void __launch_bounds__(256, 3) k_couple_tiles(CoupleArgs A) {
           const FT wt = (FT)tx.w[ix] * wyz;
           if (wt == FT(0)) continue;
           int* c = reinterpret_cast<int*>(wi + row + ix);
-          atomicAdd(c + 0, __float2int_rn(amp[0] * wt * scale[0]));
-          atomicAdd(c + 1, __float2int_rn(amp[1] * wt * scale[1]));
-          atomicAdd(c + 2, __float2int_rn(amp[2] * wt * scale[2]));
+#pragma unroll
+          for (int k = 0; k < D; ++k) atomicAdd(c + k, __float2int_rn(amp[k] * wt * scale[k]));
         }
       }
     }
   }
   __syncthreads();
   // --- 4. the window's force into the force field ---
-  float4* F = (float4*)A.F;
   for (int v = threadIdx.x; v < V; v += blockDim.x) {
     const int4 q = wi[v];
-    if (q.x == 0 && q.y == 0 && q.z == 0) continue;
-    const float4 f = make_float4((float)q.x * inv_scale[0], (float)q.y * inv_scale[1],
-                                 (float)q.z * inv_scale[2], 0.f);
+    if (q.x == 0 && q.y == 0 && (D == 2 || q.z == 0)) continue;
     int cx = bx + v % wx, cy = by + (v / wx) % wy, cz = bz + v / (wx * wy);
     if (!(lattice_coord(cx, g.n[0], g.periodic[0]) && lattice_coord(cy, g.n[1], g.periodic[1]) &&
-          lattice_coord(cz, g.n[2], g.periodic[2]))) {
+          (D == 2 || lattice_coord(cz, g.n[2], g.periodic[2])))) {
       atomicOr(A.err, ERR_INDEX);  // only zero weights fall beyond a wall
       continue;
     }
-    atomicAdd(F + cx + (long long)g.n[0] * (cy + (long long)g.n[1] * cz),
-              make_float4(f.x, f.y, f.z, 0.f));
+    const long long c = cx + (long long)g.n[0] * (cy + (long long)g.n[1] * cz);
+    if constexpr (D == 2)
+      atomicAdd(reinterpret_cast<float2*>(A.F) + c,
+                make_float2((float)q.x * inv_scale[0], (float)q.y * inv_scale[1]));
+    else
+      atomicAdd(reinterpret_cast<float4*>(A.F) + c,
+                make_float4((float)q.x * inv_scale[0], (float)q.y * inv_scale[1],
+                            (float)q.z * inv_scale[2], 0.f));
   }
 }
 
@@ -1902,6 +1930,7 @@ CoupleArgs couple_args(const State& s) {
   A.tw = P.tw;
   A.perm = P.perm;
   A.start = P.bin_cnt;
+  A.nbin = P.nbin;
   A.f = s.f[s.cur];
   A.mom = s.mom;
   A.F = s.F;
@@ -1932,7 +1961,9 @@ cudaError_t couple_t(const State& s, cudaStream_t st, int* nk, cudaEvent_t befor
     if constexpr (D == 3 && sizeof(R) == 4) {
       // 3D, FP32 arithmetic, delta interpolation, atomic spreading: by tiles
       if (!s.phy.lagrange && A.spread) {
-        k_couple_tiles<Q, W, St, FT><<<(unsigned)(P.ntiles * TILE_CHUNKS), 256, 0, st>>>(A);
+        constexpr int TPC = CoupleWindow<D, W>::TPC;
+        const long long groups = (P.ntiles + TPC - 1) / TPC;
+        k_couple_tiles<Q, W, St, FT><<<(unsigned)(groups * TILE_CHUNKS), 256, 0, st>>>(A);
         tiled = true;
       }
     }
