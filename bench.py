@@ -408,49 +408,89 @@ def run_gpu(args, rank, world):
 
 
 def ensemble_bench(args, k=None):
-    """The batched ensemble (64 independent 2D instances, 64^2..512^2, FP32):
-    K steps through one graph launch per two steps for all members, against the
-    same members stepped one after another (each through its own graphs), after
-    each member's stream-collide block shape is autotuned."""
+    """The batched ensemble (64 independent 2D instances, 64^2..512^2, FP32), K
+    steps each way:
+    - persistent: one cooperative kernel launch per 10 steps of all members
+      (replayed from a CUDA graph), launch shape autotuned on real steps first;
+      also with the default shape, and with every member keeping its cell list
+      for 10 steps;
+    - branches: one graph launch per two steps, one branch of ordinary step
+      kernels per member;
+    - one by one: each member stepped in turn through its own graphs, after each
+      member's stream-collide block shape is autotuned."""
     import torch
     from paper_1407_6704_gb300.inputs import ensemble_workloads
     from paper_1407_6704_gb300.pibm import Ensemble, Pibm
 
     ws = ensemble_workloads()
-    k = k or min(args.steps, 400)
+    k = k or min(max(args.steps, 20), 400)
     cells = sum(w.ncell for w, _ in ws)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(step, stream):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
     sims = [Pibm.from_workload(w, precision="fp32", particles=p) for w, p in ws]
     for s in sims:
         s.autotune()
         s.step(args.warmup)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for s in sims:
-        s.step(k)
-    e1.record()
-    torch.cuda.synchronize()
-    ms_seq = e0.elapsed_time(e1) / k
+
+    def one_by_one(n):
+        for s in sims:
+            s.step(n)
+
+    ms_seq = timed(one_by_one, torch.cuda.current_stream())
     ens = Ensemble(sims)
+    out = {"persistent_info": ens.info()}
+    ens.set_mode(False)
     ens.step(args.warmup + (args.warmup % 2))
-    ens.status()
-    e0.record(ens.stream)
-    ens.step(k)
-    e1.record(ens.stream)
-    torch.cuda.synchronize()
-    ms_ens = e0.elapsed_time(e1) / k
+    ms_branch = timed(ens.step, ens.stream)
+    ens.set_mode(True)
+    ens.step(max(args.warmup, 10))
+    ms_default = timed(ens.step, ens.stream)
+    l0 = ens.launch_count()
+    choice = ens.autotune(steps_per_candidate=10)
+    ens.step(10)
+    l1 = ens.launch_count()
+    ms_ens = timed(ens.step, ens.stream)
+    launches = ens.launch_count() - l1
     status = ens.status()
     ens.close()
     for s in sims:
         s.close()
-    return {"workload": "64 independent 2D D2Q9 sedimentation instances, sides 64..512 "
-                        "log-uniform, 100..20k particles, tau 0.55..1.0, ratio 1.5..3.0, "
-                        "d 0.5, 2-point delta, FP32",
-            "cells": cells, "particles": sum(w.n_particles for w, _ in ws), "steps": k,
-            "ms_per_step": ms_ens, "value": cells / (ms_ens * 1e-3) / 1e6, "unit": "MLUPS",
-            "members_one_by_one_ms_per_step": ms_seq,
-            "members_one_by_one_value": cells / (ms_seq * 1e-3) / 1e6, "status": status}
+    # every member keeping its cell list for 10 steps (persistent only)
+    sims = [Pibm.from_workload(w, precision="fp32", particles=p, rebin_every=10) for w, p in ws]
+    ens = Ensemble(sims)
+    ens.configure(choice["ctas_per_sm"], choice["cells_per_item"])
+    ens.step(max(args.warmup, 10))
+    ms_kept = timed(ens.step, ens.stream)
+    status_kept = ens.status()
+    ens.close()
+    for s in sims:
+        s.close()
+    mlups = lambda ms: cells / (ms * 1e-3) / 1e6  # noqa: E731
+    out.update({
+        "workload": "64 independent 2D D2Q9 sedimentation instances, sides 64..512 "
+                    "log-uniform, 100..20k particles, tau 0.55..1.0, ratio 1.5..3.0, "
+                    "d 0.5, 2-point delta, FP32, cell list rebuilt every step",
+        "cells": cells, "particles": sum(w.n_particles for w, _ in ws), "steps": k,
+        "mode": "persistent", "autotuned": choice, "launches_in_timed_region": launches,
+        "autotune_launches": l1 - l0,
+        "ms_per_step": ms_ens, "value": mlups(ms_ens), "unit": "MLUPS",
+        "persistent_default_shape_ms_per_step": ms_default,
+        "persistent_default_shape_value": mlups(ms_default),
+        "branches_ms_per_step": ms_branch, "branches_value": mlups(ms_branch),
+        "members_one_by_one_ms_per_step": ms_seq, "members_one_by_one_value": mlups(ms_seq),
+        "persistent_cell_list_kept_10_ms_per_step": ms_kept,
+        "persistent_cell_list_kept_10_value": mlups(ms_kept),
+        "status": status, "status_kept": status_kept})
+    return out
 
 
 def every_step_bench(args, w, X, dia, rr):

@@ -61,6 +61,9 @@ extern "C" {
 #define PIBM_ENOTSUP (-6)   /* combination not built into this library */
 #define PIBM_EINTERNAL (-7) /* a device-side index check failed; the access was skipped */
 #define PIBM_ETOOBIG (-8)   /* larger than the fixed scratch of pibm_fluid_sums_noalloc */
+#define PIBM_ETIMEOUT (-9)  /* a grid-wide barrier of the persistent ensemble kernel waited
+                               longer than its limit; the kernel returned without finishing
+                               (the members' states are then undefined) */
 
 /* lattices (value = number of velocities q) */
 #define PIBM_D2Q9 9
@@ -267,20 +270,77 @@ int pibm_autotune(pibm_t* h, int* block_xy);
 
 /* Ensembles: independent simulations (each made by pibm_create, possibly with
  * different lattices, particle counts and parameters) that advance together.
- * pibm_ensemble_step captures two steps of every member into one CUDA graph,
- * one independent branch per member, and replays it: one graph launch advances
- * every member by two steps. Members stay ordinary handles (read them with
- * pibm_read_fields etc. after pibm_ensemble_status); stepping a member on its
- * own between ensemble steps is allowed (the graph is rebuilt when needed). All
- * members must live on one device; the ensemble does not own them and must be
- * destroyed before them. Errors: PIBM_EINVAL (no members, NULL or repeated
- * member, members on different devices), PIBM_ECUDA. */
+ * Two modes, chosen by pibm_ensemble_create:
+ *  - persistent, when every member is D2Q9 with FP32 or FP64 storage (the same
+ *    for all), the same delta width, delta interpolation, linear contacts, no
+ *    DEM sub-cycling, and there are at most 256 members: one cooperative kernel
+ *    runs every phase of the coupled step (Eqs. 2-13: cell list, contacts,
+ *    moment field, interpolation, update, spreading, stream-collide) for all
+ *    members, with grid-wide barriers between the phases; a launch covers up to
+ *    10 steps, and the 10-step launch is replayed from a CUDA graph. Work items
+ *    (256 particles, a run of lattice cells, a block of tiles) are numbered per
+ *    member from offset tables and split evenly over the CTAs. A member follows
+ *    the same arithmetic as when stepped alone, with any rebin_every (each
+ *    member keeps its own cell-list period);
+ *  - branches, otherwise: pibm_ensemble_step captures two steps of every member
+ *    into one CUDA graph, one independent branch per member, and replays it;
+ *    members must then rebuild their cell list every step (rebin_every <= 1,
+ *    else PIBM_ENOTSUP).
+ * Members stay ordinary handles (read them with pibm_read_fields etc. after
+ * pibm_ensemble_status); stepping a member on its own between ensemble steps is
+ * allowed when the caller orders the two streams. All members must live on one
+ * device; the ensemble does not own them and must be destroyed before them.
+ * pibm_ensemble_create synchronises the members' streams. Errors: PIBM_EINVAL
+ * (no members, NULL or repeated member, members on different devices),
+ * PIBM_ENOTSUP, PIBM_ENOMEM (device tables of the persistent mode), PIBM_ECUDA. */
 typedef struct pibm_ensemble_t pibm_ensemble_t;
 int pibm_ensemble_create(pibm_t* const* members, int count, void* stream, pibm_ensemble_t** out);
 int pibm_ensemble_step(pibm_ensemble_t* e, int64_t nsteps);
-/* Synchronise the ensemble's stream; the first non-OK member health status. */
+/* Synchronise the ensemble's stream; PIBM_ETIMEOUT if a barrier of the
+ * persistent kernel gave up, else the first non-OK member health status. */
 int pibm_ensemble_status(pibm_ensemble_t* e);
 void pibm_ensemble_destroy(pibm_ensemble_t* e);
+/* Persistent mode only (PIBM_ENOTSUP otherwise). Launch shape: ctas_per_sm CTAs
+ * of 256 threads per SM (0: as many as fit; at most that many) and
+ * cells_per_item lattice cells per collision work item (0: unchanged; a positive
+ * multiple of 256; default 1024). Takes effect at the next launch; the graph
+ * captured before is kept only when the shape is unchanged. Errors: PIBM_EINVAL. */
+int pibm_ensemble_configure(pibm_ensemble_t* e, int ctas_per_sm, int cells_per_item);
+/* Pick the persistent launch shape by timing: every candidate (CTAs per SM x
+ * cells per item) advances the ensemble by steps_per_candidate steps (real
+ * steps: the ensemble moves on by candidates x steps_per_candidate steps in
+ * all), timed with events on the ensemble's stream; the fastest is kept.
+ * choice (may be NULL) receives {ctas_per_sm, cells_per_item, candidates}.
+ * Synchronises the stream. PIBM_ENOTSUP in branch mode. */
+int pibm_ensemble_autotune(pibm_ensemble_t* e, int steps_per_candidate, int* choice);
+/* info[6]: {1 persistent / 0 branches, CTAs per SM, largest CTAs per SM that fit,
+ * cells per collision item, CTAs of the grid, 1 when the launches replay from a
+ * CUDA graph}; entries 1-5 are 0 when the members do not qualify for the
+ * persistent mode. */
+int pibm_ensemble_info(pibm_ensemble_t* e, int* info);
+/* Switch between the persistent mode (1; PIBM_ENOTSUP when the members do not
+ * qualify) and the branch mode (0; PIBM_ENOTSUP when a member keeps its cell
+ * list, rebin_every > 1). Members keep their states; takes effect at the next
+ * pibm_ensemble_step. */
+int pibm_ensemble_set_mode(pibm_ensemble_t* e, int persistent);
+/* Persistent kernel launches made by pibm_ensemble_step so far. */
+int pibm_ensemble_launch_count(pibm_ensemble_t* e, int64_t* count);
+/* Fault injection for tests (persistent mode): in the next launch, CTA `block`
+ * does not arrive at the first grid barrier, and every barrier wait of the
+ * ensemble gives up after limit_s seconds (0 < limit_s <= 10; the limit stays).
+ * The launch then returns early, pibm_ensemble_status reports PIBM_ETIMEOUT and
+ * every later launch of the ensemble returns at once. Nothing faults or hangs. */
+int pibm_ensemble_inject_skip(pibm_ensemble_t* e, int block, double limit_s);
+
+/* Grid-barrier self-test: one cooperative launch of nblocks CTAs that pass
+ * nbarriers grid-wide barriers of the persistent kernel's kind; CTA skip_block
+ * (-1: none) does not arrive at the first one. Each wait gives up after limit_s
+ * seconds (0 < limit_s <= 10). Returns PIBM_OK when all barriers passed (*passed
+ * = nbarriers), PIBM_ETIMEOUT when a wait gave up (*passed = 0), PIBM_EINVAL when
+ * nblocks CTAs cannot all be resident at once or an argument is out of range,
+ * PIBM_ENOMEM, PIBM_ECUDA. Synchronises the device. */
+int pibm_grid_barrier_test(int nblocks, int skip_block, int nbarriers, double limit_s,
+                           int* passed);
 
 /* Free the handle (and the workspace when the library allocated it). NULL is a no-op. */
 void pibm_destroy(pibm_t* h);

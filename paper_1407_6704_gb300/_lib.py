@@ -19,6 +19,7 @@ PIBM_EESCAPED = -5
 PIBM_ENOTSUP = -6
 PIBM_EINTERNAL = -7
 PIBM_ETOOBIG = -8
+PIBM_ETIMEOUT = -9
 
 PIBM_D2Q9, PIBM_D3Q15, PIBM_D3Q19 = 9, 15, 19
 PIBM_WALL, PIBM_PERIODIC = 0, 1
@@ -37,7 +38,9 @@ EXPORTS = ["pibm_workspace_bytes", "pibm_create", "pibm_step", "pibm_forces",
            "pibm_destroy", "pibm_strerror", "pibm_profile_steps", "pibm_last_error",
            "pibm_fluid_sums_noalloc", "pibm_autotune", "pibm_ensemble_create",
            "pibm_ensemble_step", "pibm_ensemble_status", "pibm_ensemble_destroy",
-           "pibm_settling_gradient", "pibm_launch_count"]
+           "pibm_settling_gradient", "pibm_launch_count", "pibm_ensemble_configure",
+           "pibm_ensemble_autotune", "pibm_ensemble_info", "pibm_ensemble_launch_count",
+           "pibm_ensemble_inject_skip", "pibm_grid_barrier_test", "pibm_ensemble_set_mode"]
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -131,6 +134,22 @@ def load(path: str = LIB_PATH):
     L.pibm_ensemble_status.restype = ctypes.c_int
     L.pibm_ensemble_destroy.argtypes = [vp]
     L.pibm_ensemble_destroy.restype = None
+    ip = ctypes.POINTER(ctypes.c_int)
+    L.pibm_ensemble_configure.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.pibm_ensemble_configure.restype = ctypes.c_int
+    L.pibm_ensemble_autotune.argtypes = [vp, ctypes.c_int, ip]
+    L.pibm_ensemble_autotune.restype = ctypes.c_int
+    L.pibm_ensemble_info.argtypes = [vp, ip]
+    L.pibm_ensemble_info.restype = ctypes.c_int
+    L.pibm_ensemble_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    L.pibm_ensemble_launch_count.restype = ctypes.c_int
+    L.pibm_ensemble_set_mode.argtypes = [vp, ctypes.c_int]
+    L.pibm_ensemble_set_mode.restype = ctypes.c_int
+    L.pibm_ensemble_inject_skip.argtypes = [vp, ctypes.c_int, ctypes.c_double]
+    L.pibm_ensemble_inject_skip.restype = ctypes.c_int
+    L.pibm_grid_barrier_test.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         ip]
+    L.pibm_grid_barrier_test.restype = ctypes.c_int
     L.pibm_settling_gradient.argtypes = [P, ctypes.c_int64, ctypes.c_int64, vp, _dp, _dp, _dp, _dp]
     L.pibm_settling_gradient.restype = ctypes.c_int
     L.pibm_last_error.argtypes = []

@@ -6,6 +6,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -28,6 +29,7 @@ struct pibm_t {
   int debug_sync;          // synchronise after every phase (PIBM_DEBUG_SYNC=1)
   int since_rebin;         // steps since the cell list was last rebuilt (0: rebuild next)
   int64_t launches;        // kernels launched by pibm_step so far
+  int64_t nstep;           // steps taken so far (any path)
   int64_t graph_kernels;   // kernels in one replay of the step graphs
   int graph_steps;         // steps in one replay of the step graphs
   // overlap: contacts and the free tiles' collision on a second stream
@@ -194,7 +196,9 @@ Layout layout(const pibm_config* c) {
   L.rank = take(sizeof(unsigned) * np);
   L.perm = take(sizeof(unsigned) * np);
   L.bin = take(sizeof(unsigned) * (nbin + 1));
-  L.bsum = take(sizeof(unsigned) * scan_blocks);
+  // chunk totals of the cell-list scan: chunks of 8192 counts in the step kernels,
+  // of 2048 in the batched persistent kernel
+  L.bsum = take(sizeof(unsigned) * std::max<long long>(scan_blocks, (nbin + 1 + 2047) / 2048));
   const long long ntiles = nbin / bin_map(c).tc;
   L.tflag = take(np > 0 ? sizeof(int) * ntiles : 0);
   L.tbusy = take(np > 0 ? sizeof(int) * ntiles : 0);
@@ -263,6 +267,7 @@ int enqueue_step(pibm_t* h, cudaStream_t st, int* nk_out, bool split_ok = true) 
   }
   s.cur ^= 1;
   h->since_rebin = (h->since_rebin + 1) % s.phy.rebin;
+  ++h->nstep;
   if (rebuild) h->kernels_per_step = nk;
   if (nk_out) *nk_out = nk;
   return PIBM_OK;
@@ -282,6 +287,7 @@ int build_graph(pibm_t* h, int parity) {
   // where they started, so the graph can be replayed.
   cudaGraph_t g = nullptr;
   const int saved = h->s.cur, saved_r = h->since_rebin, saved_k = h->kernels_per_step;
+  const int64_t saved_n = h->nstep;
   h->s.cur = parity;
   h->since_rebin = 0;
   if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -300,6 +306,7 @@ int build_graph(pibm_t* h, int parity) {
   cudaError_t e = cudaStreamEndCapture(h->cap, &g);
   h->s.cur = saved;
   h->since_rebin = saved_r;
+  h->nstep = saved_n;
   h->kernels_per_step = saved_k > 0 ? saved_k : h->kernels_per_step;
   h->graph_kernels = total;
   h->graph_steps = len;
@@ -367,6 +374,7 @@ const char* pibm_strerror(int st) {
     case PIBM_ENOTSUP: return "configuration not supported by this build";
     case PIBM_EINTERNAL: return "internal index check failed (access skipped)";
     case PIBM_ETOOBIG: return "size exceeds the fixed static scratch of the no-allocation call";
+    case PIBM_ETIMEOUT: return "a grid barrier of the persistent ensemble kernel timed out";
     default: return "unknown status";
   }
 }
@@ -646,6 +654,7 @@ int pibm_step(pibm_t* h, int64_t nsteps) {
       }
       CK(cudaGraphLaunch(h->graph[par], h->stream));
       nsteps -= len;  // an even number of toggles leaves s.cur unchanged
+      h->nstep += len;
       h->launches += h->graph_kernels;
     } else {
       int nk = 0;
@@ -860,16 +869,29 @@ int pibm_autotune(pibm_t* h, int* block_xy) {
 }
 
 // ---------------------------------------------------------------------------
-// Ensembles: independent simulations advanced together by one graph launch.
+// Ensembles: independent simulations advanced together. Persistent mode (the
+// default where every member qualifies, ensemble.cu): one cooperative kernel runs
+// ENS_GRAPH_STEPS steps of all members per launch, replayed from a CUDA graph.
+// Branch mode: a graph with one branch of ordinary step kernels per member.
 // ---------------------------------------------------------------------------
+constexpr int ENS_GRAPH_STEPS = 10;  // steps per persistent launch in the graph
+
 struct pibm_ensemble_t {
   std::vector<pibm_t*> members;
   cudaStream_t stream;          // launch stream
   cudaStream_t origin;          // capture origin
   std::vector<cudaStream_t> lanes;
-  std::vector<int> parity;      // member parities the graph was captured for
+  std::vector<int> parity;      // member parities the branch graph was captured for
   cudaGraphExec_t graph;
   int device;
+  // persistent mode
+  int persistent;
+  EnsembleDevice* pd;
+  cudaGraphExec_t pgraph;       // one persistent launch of ENS_GRAPH_STEPS steps
+  int pgraph_failed;
+  std::vector<int64_t> seen;    // member step counts after the last ensemble step
+  int64_t launches;             // kernels launched by pibm_ensemble_step
+  int timed_out;
 };
 
 static int ensemble_capture(pibm_ensemble_t* e) {
@@ -897,9 +919,11 @@ static int ensemble_capture(pibm_ensemble_t* e) {
       break;
     }
     const int saved = m->s.cur;
+    const int64_t saved_n = m->nstep;
     rc = enqueue_step(m, ln, nullptr, false);
     if (rc == PIBM_OK) rc = enqueue_step(m, ln, nullptr, false);
     m->s.cur = saved;
+    m->nstep = saved_n;
     cudaEvent_t join = ev();
     if (rc == PIBM_OK && (!join || cudaEventRecord(join, ln) != cudaSuccess ||
                           cudaStreamWaitEvent(e->origin, join, 0) != cudaSuccess))
@@ -924,19 +948,50 @@ static int ensemble_capture(pibm_ensemble_t* e) {
   return PIBM_OK;
 }
 
+// Persistent mode: the graph of one launch of ENS_GRAPH_STEPS steps. The kernel
+// reads each member's buffer parity and rebuild phase from the device table and
+// advances it, so the graph replays from any phase.
+static int ensemble_capture_persistent(pibm_ensemble_t* e) {
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(e->origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return PIBM_ECUDA;
+  }
+  const cudaError_t le = ensemble_device_launch(e->pd, ENS_GRAPH_STEPS, e->origin);
+  const cudaError_t ee = cudaStreamEndCapture(e->origin, &g);
+  if (le != cudaSuccess || ee != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return PIBM_ECUDA;
+  }
+  const cudaError_t ie = cudaGraphInstantiate(&e->pgraph, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    e->pgraph = nullptr;
+    cudaGetLastError();
+    return PIBM_ECUDA;
+  }
+  return PIBM_OK;
+}
+
 int pibm_ensemble_create(pibm_t* const* members, int count, void* stream, pibm_ensemble_t** out) {
   if (!members || count <= 0 || !out) return PIBM_EINVAL;
   *out = nullptr;
   int dev = -1;
+  std::vector<const State*> st((size_t)count);
   for (int i = 0; i < count; ++i) {
     if (!members[i]) return PIBM_EINVAL;
-    if (members[i]->s.phy.rebin > 1) return PIBM_ENOTSUP;  // members rebuild every step
     if (i == 0) dev = members[i]->device;
     if (members[i]->device != dev) return PIBM_EINVAL;
     for (int j = 0; j < i; ++j)
       if (members[j] == members[i]) return PIBM_EINVAL;
+    st[i] = &members[i]->s;
   }
   DeviceGuard guard(dev);
+  const bool persistent = ensemble_persistent_supported(st.data(), count);
+  if (!persistent)
+    for (int i = 0; i < count; ++i)
+      if (members[i]->s.phy.rebin > 1) return PIBM_ENOTSUP;  // branch mode: rebuild every step
   pibm_ensemble_t* e = new (std::nothrow) pibm_ensemble_t();
   if (!e) return PIBM_ENOMEM;
   e->members.assign(members, members + count);
@@ -945,29 +1000,83 @@ int pibm_ensemble_create(pibm_t* const* members, int count, void* stream, pibm_e
   e->graph = nullptr;
   e->device = dev;
   e->origin = nullptr;
+  e->seen.assign(count, -1);
   if (cudaStreamCreateWithFlags(&e->origin, cudaStreamNonBlocking) != cudaSuccess) {
     delete e;
     return PIBM_ECUDA;
   }
-  e->lanes.assign(count, nullptr);
-  for (int i = 0; i < count; ++i)
-    if (cudaStreamCreateWithFlags(&e->lanes[i], cudaStreamNonBlocking) != cudaSuccess) {
-      pibm_ensemble_destroy(e);
-      return PIBM_ECUDA;
-    }
   // members' own streams must be idle before the ensemble takes over
   for (int i = 0; i < count; ++i)
     if (cudaStreamSynchronize(members[i]->stream) != cudaSuccess) {
       pibm_ensemble_destroy(e);
       return PIBM_ECUDA;
     }
+  if (persistent) {
+    const int rc = ensemble_device_create(st.data(), count, dev, &e->pd);
+    if (rc != PIBM_OK) {
+      pibm_ensemble_destroy(e);
+      return rc;
+    }
+    e->persistent = 1;
+  } else {
+    e->lanes.assign(count, nullptr);
+    for (int i = 0; i < count; ++i)
+      if (cudaStreamCreateWithFlags(&e->lanes[i], cudaStreamNonBlocking) != cudaSuccess) {
+        pibm_ensemble_destroy(e);
+        return PIBM_ECUDA;
+      }
+  }
   *out = e;
+  return PIBM_OK;
+}
+
+static int ensemble_step_persistent(pibm_ensemble_t* e, int64_t nsteps) {
+  const int n = (int)e->members.size();
+  // a member stepped on its own since the last ensemble step: load the phase
+  // table from the handles again (and clear the counts a rebuild expects)
+  bool stale = false;
+  for (int i = 0; i < n; ++i) stale |= e->seen[i] != e->members[i]->nstep;
+  if (stale) {
+    std::vector<int> cur(n), sr(n);
+    for (int i = 0; i < n; ++i) {
+      cur[i] = e->members[i]->s.cur;
+      sr[i] = e->members[i]->since_rebin;
+    }
+    CK(ensemble_device_set_phase(e->pd, cur.data(), sr.data(), e->stream));
+  }
+  auto advance = [&](int k) {
+    for (int i = 0; i < n; ++i) {
+      pibm_t* m = e->members[i];
+      m->s.cur ^= (k & 1);
+      m->since_rebin = (int)((m->since_rebin + (int64_t)k) % m->s.phy.rebin);
+      m->nstep += k;
+      e->seen[i] = m->nstep;
+    }
+    e->launches += 1;
+  };
+  while (nsteps > 0) {
+    if (nsteps >= ENS_GRAPH_STEPS && !e->pgraph_failed && !ensemble_device_injected(e->pd)) {
+      if (!e->pgraph && ensemble_capture_persistent(e) != PIBM_OK) {
+        e->pgraph_failed = 1;  // launch directly from now on
+        continue;
+      }
+      CK(cudaGraphLaunch(e->pgraph, e->stream));
+      advance(ENS_GRAPH_STEPS);
+      nsteps -= ENS_GRAPH_STEPS;
+    } else {
+      const int k = (int)std::min<int64_t>(nsteps, ENS_GRAPH_STEPS);
+      CK(ensemble_device_launch(e->pd, k, e->stream));
+      advance(k);
+      nsteps -= k;
+    }
+  }
   return PIBM_OK;
 }
 
 int pibm_ensemble_step(pibm_ensemble_t* e, int64_t nsteps) {
   if (!e || nsteps < 0) return PIBM_EINVAL;
   DeviceGuard guard(e->device);
+  if (e->persistent) return ensemble_step_persistent(e, nsteps);
   while (nsteps > 0) {
     if (nsteps >= 2) {
       bool stale = !e->graph;
@@ -980,6 +1089,7 @@ int pibm_ensemble_step(pibm_ensemble_t* e, int64_t nsteps) {
         if (rc != PIBM_OK) return rc;
       }
       CK(cudaGraphLaunch(e->graph, e->stream));
+      for (pibm_t* m : e->members) m->nstep += 2;
       nsteps -= 2;
     } else {
       for (pibm_t* m : e->members) {
@@ -992,10 +1102,127 @@ int pibm_ensemble_step(pibm_ensemble_t* e, int64_t nsteps) {
   return PIBM_OK;
 }
 
+int pibm_ensemble_configure(pibm_ensemble_t* e, int ctas_per_sm, int cells_per_item) {
+  if (!e) return PIBM_EINVAL;
+  if (!e->pd) return PIBM_ENOTSUP;
+  DeviceGuard guard(e->device);
+  int before[4], after[4];
+  ensemble_device_shape(e->pd, &before[0], &before[1], &before[2], &before[3]);
+  const int rc = ensemble_device_configure(e->pd, ctas_per_sm, cells_per_item, e->stream);
+  if (rc != PIBM_OK) return rc;
+  ensemble_device_shape(e->pd, &after[0], &after[1], &after[2], &after[3]);
+  if ((before[0] != after[0] || before[2] != after[2]) && e->pgraph) {
+    CK(cudaStreamSynchronize(e->stream));  // the graph may still be running
+    cudaGraphExecDestroy(e->pgraph);
+    e->pgraph = nullptr;
+  }
+  return PIBM_OK;
+}
+
+int pibm_ensemble_autotune(pibm_ensemble_t* e, int steps_per_candidate, int* choice) {
+  if (!e || steps_per_candidate < 1) return PIBM_EINVAL;
+  if (!e->persistent) return PIBM_ENOTSUP;
+  DeviceGuard guard(e->device);
+  int per_sm = 0, max_per_sm = 0, cpi = 0;
+  ensemble_device_shape(e->pd, &per_sm, &max_per_sm, &cpi, nullptr);
+  static const int cpis[] = {256, 512, 1024, 2048, 4096};
+  // timed steps per candidate: whole graph launches
+  const int64_t timed = (steps_per_candidate + ENS_GRAPH_STEPS - 1) / ENS_GRAPH_STEPS *
+                        (int64_t)ENS_GRAPH_STEPS;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return PIBM_ECUDA;
+  }
+  int rc = PIBM_OK, best_p = per_sm, best_c = cpi, ncand = 0;
+  float best_ms = 0.f;
+  for (int p = 1; p <= max_per_sm && rc == PIBM_OK; ++p)
+    for (int c : cpis) {
+      if ((rc = pibm_ensemble_configure(e, p, c)) != PIBM_OK) break;
+      // one untimed launch captures this shape's graph and warms up
+      if ((rc = ensemble_step_persistent(e, ENS_GRAPH_STEPS)) != PIBM_OK) break;
+      float ms = 0.f;
+      cudaError_t te = cudaEventRecord(e0, e->stream);
+      if (te == cudaSuccess) rc = ensemble_step_persistent(e, timed);
+      if (rc != PIBM_OK) break;
+      if (te != cudaSuccess || (te = cudaEventRecord(e1, e->stream)) != cudaSuccess ||
+          (te = cudaEventSynchronize(e1)) != cudaSuccess ||
+          (te = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) {
+        record_error("ensemble autotune timing", te);
+        rc = PIBM_ECUDA;
+        break;
+      }
+      ++ncand;
+      if (ncand == 1 || ms < best_ms) {
+        best_ms = ms;
+        best_p = p;
+        best_c = c;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != PIBM_OK) return rc;
+  if ((rc = pibm_ensemble_configure(e, best_p, best_c)) != PIBM_OK) return rc;
+  if (choice) {
+    choice[0] = best_p;
+    choice[1] = best_c;
+    choice[2] = ncand;
+  }
+  return pibm_ensemble_status(e);
+}
+
+int pibm_ensemble_set_mode(pibm_ensemble_t* e, int persistent) {
+  if (!e || (persistent != 0 && persistent != 1)) return PIBM_EINVAL;
+  DeviceGuard guard(e->device);
+  if (persistent == e->persistent) return PIBM_OK;
+  if (persistent) {
+    if (!e->pd) return PIBM_ENOTSUP;
+    e->seen.assign(e->members.size(), -1);  // reload the phase table at the next step
+  } else {
+    for (pibm_t* m : e->members)
+      if (m->s.phy.rebin > 1) return PIBM_ENOTSUP;
+    if (e->lanes.empty()) {
+      e->lanes.assign(e->members.size(), nullptr);
+      for (auto& ln : e->lanes) CK(cudaStreamCreateWithFlags(&ln, cudaStreamNonBlocking));
+    }
+  }
+  e->persistent = persistent;
+  return PIBM_OK;
+}
+
+int pibm_ensemble_inject_skip(pibm_ensemble_t* e, int block, double limit_s) {
+  if (!e) return PIBM_EINVAL;
+  if (!e->pd) return PIBM_ENOTSUP;
+  return ensemble_device_inject(e->pd, block, limit_s);
+}
+
+int pibm_ensemble_info(pibm_ensemble_t* e, int* info) {
+  if (!e || !info) return PIBM_EINVAL;
+  for (int k = 0; k < 6; ++k) info[k] = 0;
+  info[0] = e->persistent;
+  if (e->pd) {
+    ensemble_device_shape(e->pd, &info[1], &info[2], &info[3], &info[4]);
+    info[5] = e->pgraph_failed ? 0 : 1;
+  }
+  return PIBM_OK;
+}
+
+int pibm_ensemble_launch_count(pibm_ensemble_t* e, int64_t* count) {
+  if (!e || !count) return PIBM_EINVAL;
+  *count = e->launches;
+  return PIBM_OK;
+}
+
 int pibm_ensemble_status(pibm_ensemble_t* e) {
   if (!e) return PIBM_EINVAL;
   DeviceGuard guard(e->device);
   CK(cudaStreamSynchronize(e->stream));
+  if (e->pd) {
+    const int t = ensemble_device_timed_out(e->pd, e->stream, nullptr);
+    if (t < 0) return PIBM_ECUDA;
+    if (t > 0) return PIBM_ETIMEOUT;
+  }
   int worst = PIBM_OK;
   for (pibm_t* m : e->members) {
     int rc = health(m);
@@ -1009,6 +1236,8 @@ void pibm_ensemble_destroy(pibm_ensemble_t* e) {
   DeviceGuard guard(e->device);
   if (e->stream) cudaStreamSynchronize(e->stream);
   if (e->graph) cudaGraphExecDestroy(e->graph);
+  if (e->pgraph) cudaGraphExecDestroy(e->pgraph);
+  ensemble_device_destroy(e->pd);
   for (cudaStream_t s : e->lanes)
     if (s) cudaStreamDestroy(s);
   if (e->origin) cudaStreamDestroy(e->origin);
@@ -1047,6 +1276,7 @@ int pibm_profile_steps(pibm_t* h, int64_t nsteps, double* phase_ms) {
         break;
       }
       s.cur ^= 1;
+      ++h->nstep;
     }
     if (rc == PIBM_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = PIBM_ECUDA;
     for (int64_t i = 0; i < nsteps && rc == PIBM_OK; ++i) {

@@ -212,16 +212,20 @@ __device__ __forceinline__ void add_force(FT* __restrict__ F, long long c, const
   }
 }
 
-// The moment field is read only after the kernel that writes it has finished,
-// so the loads take the read-only path.
-template <typename R>
+// In the single-simulation kernels the moment field is read only after the
+// kernel that writes it has finished, so the loads take the read-only path
+// (NC). A persistent kernel that writes the field in one phase and reads it in
+// the next must use coherent loads (NC = false).
+template <typename R, bool NC = true>
 __device__ __forceinline__ void load_moments(const R* __restrict__ mom, long long c, R (&m)[4]) {
   if constexpr (sizeof(R) == 4) {
-    const float4 a = __ldg(reinterpret_cast<const float4*>(mom) + c);
+    const float4* p = reinterpret_cast<const float4*>(mom) + c;
+    const float4 a = NC ? __ldg(p) : *p;
     m[0] = a.x; m[1] = a.y; m[2] = a.z; m[3] = a.w;
   } else {
-    const double2 a = __ldg(reinterpret_cast<const double2*>(mom) + 2 * c);
-    const double2 b = __ldg(reinterpret_cast<const double2*>(mom) + 2 * c + 1);
+    const double2* p = reinterpret_cast<const double2*>(mom) + 2 * c;
+    const double2 a = NC ? __ldg(p) : p[0];
+    const double2 b = NC ? __ldg(p + 1) : p[1];
     m[0] = a.x; m[1] = a.y; m[2] = b.x; m[3] = b.y;
   }
 }
@@ -512,6 +516,32 @@ struct HandleView {
   cudaStream_t stream;
 };
 HandleView handle_view(pibm_t* h);
+
+// Batched persistent step (ensemble.cu). The members must all be D2Q9 with
+// FP32 or FP64 storage (the same for all), the same delta width, delta
+// interpolation, linear contacts and no DEM sub-cycling.
+constexpr int ENSEMBLE_PERSISTENT_MAX = 256;  // members
+struct EnsembleDevice;
+bool ensemble_persistent_supported(const State* const* s, int n);
+int ensemble_device_create(const State* const* s, int n, int device, EnsembleDevice** out);
+void ensemble_device_destroy(EnsembleDevice* e);
+// CTAs per SM (0: as many as fit) and cells per collision item (0: unchanged;
+// a multiple of 256).
+int ensemble_device_configure(EnsembleDevice* e, int per_sm, int cpi, cudaStream_t st);
+void ensemble_device_shape(const EnsembleDevice* e, int* per_sm, int* max_per_sm, int* cpi,
+                           int* grid);
+// Load each member's buffer parity and steps since its last rebuild into the
+// device phase table, and clear the cell-list counts of members about to rebuild.
+cudaError_t ensemble_device_set_phase(EnsembleDevice* e, const int* cur, const int* sr,
+                                      cudaStream_t st);
+cudaError_t ensemble_device_launch(EnsembleDevice* e, int nsteps, cudaStream_t st);
+// Test hook: CTA `block` skips the first barrier of the next launch, every wait of
+// that launch gives up after limit_s seconds.
+int ensemble_device_inject(EnsembleDevice* e, int block, double limit_s);
+bool ensemble_device_injected(const EnsembleDevice* e);
+// 1 when a barrier wait gave up (where: its index in the launch), 0 if not, -1 on
+// a CUDA error. Synchronises st.
+int ensemble_device_timed_out(EnsembleDevice* e, cudaStream_t st, unsigned* where);
 
 // Record a failed CUDA call for pibm_last_error (this thread).
 void record_cuda_error(const char* what, cudaError_t e);

@@ -130,6 +130,10 @@ class Pibm:
         return self._L.pibm_kernels_per_step(self._h)
 
     @property
+    def set_mode(self, persistent):
+        check(self._L.pibm_ensemble_set_mode(self._h, 1 if persistent else 0),
+              "pibm_ensemble_set_mode")
+
     def launch_count(self):
         """Kernels launched by step() on this handle so far."""
         n = ctypes.c_int64()
@@ -218,8 +222,10 @@ class Pibm:
 
 
 class Ensemble:
-    """Independent simulations advanced together: one CUDA graph launch steps
-    every member twice (one graph branch per member)."""
+    """Independent simulations advanced together. Persistent mode (members of
+    one kind, see ``pibm_ensemble_create``): one cooperative kernel launch runs
+    up to 10 steps of every member, replayed from a CUDA graph; otherwise one
+    graph branch per member."""
 
     def __init__(self, members, stream=None):
         import torch
@@ -240,6 +246,40 @@ class Ensemble:
 
     def status(self):
         return self._L.pibm_ensemble_status(self._h)
+
+    def info(self):
+        """{persistent, ctas_per_sm, max_ctas_per_sm, cells_per_item, grid, graph}."""
+        out = (ctypes.c_int * 6)()
+        check(self._L.pibm_ensemble_info(self._h, out), "pibm_ensemble_info")
+        keys = ("persistent", "ctas_per_sm", "max_ctas_per_sm", "cells_per_item", "grid", "graph")
+        return dict(zip(keys, list(out)))
+
+    def configure(self, ctas_per_sm=0, cells_per_item=0):
+        check(self._L.pibm_ensemble_configure(self._h, int(ctas_per_sm), int(cells_per_item)),
+              "pibm_ensemble_configure")
+
+    def autotune(self, steps_per_candidate=20):
+        """Time every launch shape on real steps (the ensemble advances by
+        candidates x (steps, rounded up to 10, + 10) steps); keep the fastest."""
+        out = (ctypes.c_int * 3)()
+        check(self._L.pibm_ensemble_autotune(self._h, int(steps_per_candidate), out),
+              "pibm_ensemble_autotune")
+        return {"ctas_per_sm": out[0], "cells_per_item": out[1], "candidates": out[2]}
+
+    def set_mode(self, persistent):
+        check(self._L.pibm_ensemble_set_mode(self._h, 1 if persistent else 0),
+              "pibm_ensemble_set_mode")
+
+    def launch_count(self):
+        n = ctypes.c_int64()
+        check(self._L.pibm_ensemble_launch_count(self._h, ctypes.byref(n)),
+              "pibm_ensemble_launch_count")
+        return n.value
+
+    def inject_skip(self, block, limit_s):
+        """Test hook: CTA `block` skips the first barrier of the next launch."""
+        check(self._L.pibm_ensemble_inject_skip(self._h, int(block), float(limit_s)),
+              "pibm_ensemble_inject_skip")
 
     def close(self):
         if getattr(self, "_h", None):
@@ -335,3 +375,13 @@ def settling_velocity(tau, density_ratio, x0, **spec):
     """Differentiable mean settling velocity (see ``settling_gradient``) of CPU
     FP64 tensors tau (0-d), density_ratio (n,), x0 (n, d)."""
     return _settling_function().apply(tau, density_ratio, x0, spec)
+
+
+def grid_barrier_test(nblocks, skip_block=-1, nbarriers=1, limit_s=0.2):
+    """Run the persistent kernel's grid barrier in a cooperative launch of
+    nblocks CTAs (``pibm_grid_barrier_test``); returns (status, barriers passed)."""
+    L = _lib.load()
+    passed = ctypes.c_int()
+    st = L.pibm_grid_barrier_test(int(nblocks), int(skip_block), int(nbarriers), float(limit_s),
+                                  ctypes.byref(passed))
+    return st, passed.value
