@@ -130,10 +130,6 @@ class Pibm:
         return self._L.pibm_kernels_per_step(self._h)
 
     @property
-    def set_mode(self, persistent):
-        check(self._L.pibm_ensemble_set_mode(self._h, 1 if persistent else 0),
-              "pibm_ensemble_set_mode")
-
     def launch_count(self):
         """Kernels launched by step() on this handle so far."""
         n = ctypes.c_int64()
