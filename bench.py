@@ -49,10 +49,12 @@ def _peaks():
 
 
 def _src_hash(source):
-    """Hash of the source file that defines a kernel (csrc/<source>)."""
+    """Hash of the source files that define a kernel (csrc/<source>, or a list of
+    such names hashed in order)."""
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1407_6704_gb300", "csrc", source), "rb") as fh:
-        h.update(fh.read())
+    for name in ([source] if isinstance(source, str) else source):
+        with open(os.path.join(ROOT, "paper_1407_6704_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -166,10 +168,25 @@ def stencil_cells(X, n, width):
     return int(np.unique(ids).size)
 
 
-def collide_flops_per_cell_fp64(q):
-    # FP64 operations of the fused collision (counted from the kernel's arithmetic:
-    # moments, velocity, per-pair relaxation); used for the ALU roofline of FP64
-    return {9: 91, 15: 150, 19: 185}[q]
+FP64_OPS_FILE = os.path.join(ROOT, "profiles", "fp64_collide_ops.json")
+
+
+def collide_fp64_ops(q):
+    """FP64 flops per cell of the fused collision (FMA = 2) and the ceiling of
+    its instruction mix on the FP64 pipe (2 instructions per clock per SM): from
+    the committed ncu instruction counts for D2Q9, else an estimate from the
+    kernel's arithmetic scaled by q (marked as such)."""
+    try:
+        with open(FP64_OPS_FILE) as fh:
+            ent = json.load(fh)["d2q9"]
+        pc = ent["per_cell"]
+        fl, ins, src = pc["flops"], pc["instructions"], "ncu instruction counts"
+    except Exception:
+        fl, ins, src = 136, 95, "estimate"
+    if q != 9:
+        fl, ins, src = fl * q / 9.0, ins * q / 9.0, "D2Q9 counts scaled by q/9 (estimate)"
+    ceiling = 2.0 * (fl / ins) * 152 * 2.07e9 / 1e12
+    return fl, ceiling, src
 
 
 def max_over_ranks(v, dist, device="cuda"):
@@ -321,12 +338,14 @@ def run_gpu(args, rank, world):
             v["achieved_gbs_with_stencil_cells"] = v["bytes_with_stencil_cells"] / (v["ms"] * 1e-3) / 1e9
     dom = max(kern, key=lambda k: kern[k]["ms"])
     if prec == "fp64" and dom == "collide_stream":
-        flops = cells * collide_flops_per_cell_fp64(w.q)
-        ach = flops / (ph["collide_stream"] * 1e-3) / 1e12
+        fpc, ceil_, src = collide_fp64_ops(w.q)
+        ach = cells * fpc / (ph["collide_stream"] * 1e-3) / 1e12
         roof = {"kernel": "k_collide_stream", "bound": "alu", "achieved": ach,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
                 "traffic": _traffic("k_collide_stream", f"{args.workload}-{prec}"),
-                "peak_source": "nominal FP64 rate (2 FMA/clk/SM x 152 SMs x 2.07 GHz)"}
+                "peak_source": "nominal FP64 rate (2 FMA/clk/SM x 152 SMs x 2.07 GHz)",
+                "flops_per_cell": fpc, "flops_source": src,
+                "mix_ceiling_tflops": ceil_, "frac_of_mix_ceiling": ach / ceil_}
     else:
         kk = dom if kern[dom]["bytes"] else "collide_stream"
         ach = kern[kk]["achieved_gbs"]
@@ -382,11 +401,14 @@ def run_gpu(args, rank, world):
                    "value": world * cells / (rr_["ms"] * 1e-3) / 1e6, "unit": "MLUPS",
                    "phases_ms_per_step": rr_["phases"], "status": rr_["status"]}
         if p == "fp64":
-            fl = cells * collide_flops_per_cell_fp64(w.q)
-            a = fl / (rr_["phases"]["collide_stream"] * 1e-3) / 1e12
+            fpc, ceil_, src = collide_fp64_ops(w.q)
+            a = cells * fpc / (rr_["phases"]["collide_stream"] * 1e-3) / 1e12
             line[p]["collide_roofline"] = {"bound": "alu", "achieved": a,
                                            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                                           "frac": a / FP64_PEAK_TFLOPS}
+                                           "frac": a / FP64_PEAK_TFLOPS,
+                                           "flops_per_cell": fpc, "flops_source": src,
+                                           "mix_ceiling_tflops": ceil_,
+                                           "frac_of_mix_ceiling": a / ceil_}
     # the secondary measurements and the CPU baseline belong to the single-GPU run;
     # a multi-rank (scaling) run reports its replicas' throughput only
     solo = world == 1
@@ -806,6 +828,28 @@ def run_profile_only(args):
 
     build.build()
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    if args.workload == "ensemble":
+        # the 64-member ensemble through the persistent kernel (10 steps a launch)
+        from paper_1407_6704_gb300.inputs import ensemble_workloads
+        from paper_1407_6704_gb300.pibm import Ensemble
+        sims = [Pibm.from_workload(w, precision="fp32", particles=p, rebin_every=args.rebin)
+                for w, p in ensemble_workloads()]
+        ens = Ensemble(sims)
+        ens.step(args.warmup)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(ens.stream)
+        ens.step(args.steps)
+        e1.record(ens.stream)
+        torch.cuda.synchronize()
+        print(json.dumps({"workload": "ensemble", "info": ens.info(),
+                          "ms_per_step": e0.elapsed_time(e1) / args.steps,
+                          "status": ens.status()}))
+        ens.close()
+        for s_ in sims:
+            s_.close()
+        return
     w = preset(args.workload)
     X, dia, rr = workload_particles(w)
     sim = Pibm.from_workload(w, precision=args.precision, particles=(X, dia, rr),
