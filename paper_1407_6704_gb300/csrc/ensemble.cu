@@ -397,9 +397,16 @@ __global__ void __launch_bounds__(ENS_THREADS, EnsShape<Q, St>::MINB) k_ensemble
         } else {
           const long long i = t - tp;
           const int m = item_pos_shared(s_moff, E.nm, i);
+          // the arguments by value: stores to the moment field could alias a
+          // struct read in place, which would force reloads of every field
           const CoupleArgs& Am = E.mem[m].A[s_cur[m] ^ (k & 1)];
-          moments_block<Q, St>(Am.g, Am.bm, E.mem[m].x.tbusy, E.mem[m].x.tn, (const T*)Am.f,
-                               (R*)Am.mom, (int)(i - s_moff[m]));
+          const Geometry g = Am.g;
+          const BinMap bm = Am.bm;
+          const T* f = (const T*)Am.f;
+          R* mom = (R*)Am.mom;
+          const int* tbusy = E.mem[m].x.tbusy;
+          const unsigned* tn = E.mem[m].x.tn;
+          moments_block<Q, St>(g, bm, tbusy, tn, f, mom, (int)(i - s_moff[m]));
         }
       });
     }
@@ -442,9 +449,12 @@ __global__ void __launch_bounds__(ENS_THREADS, EnsShape<Q, St>::MINB) k_ensemble
       const unsigned n0 = (unsigned)sA.g.n[0], n1 = (unsigned)sA.g.n[1];
       const int* flag = s_np[m] ? sX.tflag : nullptr;
       using TD = TileDims<D>;
+      // the thread's cells c0 + tid + 256 j; (x, y, z) of the first by division
+      // (ncell < 2^31), then stepped along x with carries into y and z
+      unsigned r0 = (unsigned)(c0 + tid) / n0;
+      int x = (int)((unsigned)(c0 + tid) - r0 * n0), y = (int)(r0 % n1), z = (int)(r0 / n1);
       for (long long c = c0 + tid; c < c1; c += ENS_THREADS) {
-        const unsigned cu = (unsigned)c, r = cu / n0;  // ncell < 2^31
-        const int x = (int)(cu - r * n0), y = (int)(r % n1), z = (int)(r / n1);
+        const unsigned cu = (unsigned)c;
         // no particle stencil reaches a cell of a free tile of the cell list, so
         // its force is zero and stays untouched (as in the single-simulation
         // step's free-tile collision)
@@ -455,6 +465,14 @@ __global__ void __launch_bounds__(ENS_THREADS, EnsShape<Q, St>::MINB) k_ensemble
         if (busy) take_force<D, FT, R>((FT*)sA.F, (long long)cu, Fv);
         collide_store<Q, St>((T*)sX.fout[cur], sA.g, (long long)cu, sv, Fv, (R)sA.ph.omega,
                              (R)sA.ph.cF, sA.err);
+        x += ENS_THREADS;
+        while (x >= (int)n0) {
+          x -= (int)n0;
+          if (++y == (int)n1) {
+            y = 0;
+            ++z;
+          }
+        }
       }
       if (s_np[m] && phase_of(m, k + 1) == 0) {
         const long long n = sA.nbin + 1;
