@@ -182,8 +182,11 @@ Layout layout(const pibm_config* c) {
   L.ti = take(c->deterministic ? sizeof(int) * 12 * np : 0);
   L.tw = take(c->deterministic ? sizeof(double) * 12 * np : 0);
   const bool keep = c->rebin_every > 1;
-  L.nb = take(keep ? sizeof(unsigned) * (d == 2 ? 24 : 64) * np : 0);
-  L.nbn = take(keep ? sizeof(int) * np : 0);
+  // contact candidates recorded at a rebuild (kept cell list) or at the first DEM
+  // sub-step (sub-cycling)
+  const bool record = keep || sub;
+  L.nb = take(record ? sizeof(unsigned) * (d == 2 ? 24 : 64) * np : 0);
+  L.nbn = take(record ? sizeof(int) * np : 0);
   L.xs0 = take(keep ? sizeof(float4) * np : 0);
   L.xr = take(sizeof(float4) * np);
   L.cr = take(sizeof(int4) * np);

@@ -97,11 +97,15 @@ cudaError_t couple_t(const State& s, cudaStream_t st, int* nk, cudaEvent_t befor
     else
       k_sub_init<Q, W, St, false><<<pb, 256, 0, st>>>(A);
     const double h = 1.0 / (double)s.phy.substeps;
+    // the first sub-step records the contact candidates, the others reuse them
     for (int k = 0; k < s.phy.substeps; ++k) {
-      if (s.phy.hertz)
-        k_contacts<D, true, true, 0><<<pb, 256, 0, st>>>(A);
-      else
-        k_contacts<D, true, false, 0><<<pb, 256, 0, st>>>(A);
+      if (s.phy.hertz) {
+        if (k == 0) k_contacts<D, true, true, 1><<<pb, 256, 0, st>>>(A);
+        else k_contacts<D, true, true, 2><<<pb, 256, 0, st>>>(A);
+      } else {
+        if (k == 0) k_contacts<D, true, false, 1><<<pb, 256, 0, st>>>(A);
+        else k_contacts<D, true, false, 2><<<pb, 256, 0, st>>>(A);
+      }
       k_substep<D><<<pb, 256, 0, st>>>(A, h);
     }
     n += 1 + 2 * s.phy.substeps;

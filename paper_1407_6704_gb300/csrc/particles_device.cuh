@@ -638,10 +638,12 @@ __device__ __forceinline__ void contacts_at(const CoupleArgs& A, long long sl) {
   const float rpf = me.w;
   const int bc[3] = {mc.x, mc.y, mc.z};
   double Fc[3] = {0.0, 0.0, 0.0};
-  // the contact force of the candidate at slot s2
-  auto consider = [&](unsigned s2) {
+  // FP32 screen of the candidate at slot s2 (positions of the step start, so the
+  // same answer at every sub-step)
+  auto screen = [&](unsigned s2, unsigned& q) {
     const float4 o = A.xs[s2];
     const int4 oc = A.cs[s2];
+    q = (unsigned)oc.w;
     const float oq[3] = {o.x, o.y, o.z};
     const int cq[3] = {oc.x, oc.y, oc.z};
     float d2f = 0.f;
@@ -657,8 +659,12 @@ __device__ __forceinline__ void contacts_at(const CoupleArgs& A, long long sl) {
       d2f += s * s;
     }
     const float reach = rpf + o.w + mrg;
-    if (d2f > reach * reach) return;
-    const unsigned q = (unsigned)oc.w;
+    return d2f <= reach * reach;
+  };
+  // the contact force of the candidate at slot s2
+  auto consider = [&](unsigned s2) {
+    unsigned q;
+    if (!screen(s2, q)) return;
     // FP64 overlap test and force
     if (q >= (unsigned)np) {
       atomicOr(A.err, ERR_INDEX);
@@ -709,7 +715,11 @@ __device__ __forceinline__ void contacts_at(const CoupleArgs& A, long long sl) {
     return d2f <= reach * reach;
   };
   // NB: 0 traverse the cells, 1 traverse and record the candidates, 2 take the
-  // recorded candidates (traversing when they did not fit)
+  // recorded candidates (traversing when they did not fit). Kept cell list: the
+  // record of a rebuild holds the pairs that can touch before the next rebuild.
+  // Sub-cycling (SUB): the record of the first sub-step holds the pairs that pass
+  // the FP32 screen, whose answer does not change over the step's sub-steps, so
+  // every later sub-step sees the same candidates in the same order.
   if (NB == 2 && A.nbn[sl] >= 0) {
     // the candidates the traversal of the last rebuild recorded, in its order
     const int cnt = A.nbn[sl];
@@ -748,7 +758,8 @@ __device__ __forceinline__ void contacts_at(const CoupleArgs& A, long long sl) {
           }
           for (unsigned s2 = lo; s2 < hi; ++s2) {
             if (s2 == (unsigned)sl) continue;
-            if (rec && near_at_rebuild(s2)) {
+            unsigned q_;
+            if (rec && (SUB ? screen(s2, q_) : near_at_rebuild(s2))) {
               if (nrec < A.nb_max) A.nb[(long long)nrec * np + sl] = s2;
               ++nrec;
             }
