@@ -377,7 +377,10 @@ def run_gpu(args, rank, world):
         "data": "synthetic (seeded uniform non-overlapping particles, fluid at rest)",
         "config": {"workload": WORKLOAD_DESC, "lattice": "D2Q9", "n": list(w.n),
                    "particles": w.n_particles, "precision": prec,
-                   "particle_state": "f64", "parallelism": f"replicas x{world}",
+                   "particle_state": "f64",
+                   "particle_update": "f64 (U' - U and g formed in FP64; the FP32-formed "
+                                      "update is timed under variants.particle_update_fp32)",
+                   "parallelism": f"replicas x{world}",
                    "cell_list_rebuild_every": args.rebin,
                    "overlap": "auto: on for this 2D lattice (contacts and the particle-free "
                               "tiles' collision on a second stream)",
@@ -554,6 +557,7 @@ def _timed_steps(sim, warmup, steps):
 
 def variants_bench(args, w, X, dia, rr, steps=200):
     """The paper's variants on the headline workload (c2, FP32 storage): the
+    particle update formed in FP32 (the headline forms it in FP64), the
     4-point Lagrange interpolant (Eq. 5), the Hertz normal contact (Eq. 15, E = 0.1,
     nu = 0.3 in lattice units), and Hertz with 4 DEM sub-steps per fluid step (with
     the every-step cell list that sub-cycling needs). A variant that fails reports
@@ -562,6 +566,8 @@ def variants_bench(args, w, X, dia, rr, steps=200):
     from paper_1407_6704_gb300.pibm import Pibm
 
     specs = {
+        # the headline configuration with the particle update formed in FP32
+        "particle_update_fp32": dict(particle_update="fp32", rebin_every=args.rebin),
         "lagrange4": dict(interp="lagrange4", rebin_every=args.rebin),
         "hertz": dict(contact="hertz", young=0.1, poisson=0.3, rebin_every=args.rebin),
         "hertz_substeps4": dict(contact="hertz", young=0.1, poisson=0.3, substeps=4,

@@ -65,6 +65,10 @@ extern "C" {
                                longer than its limit; the kernel returned without finishing
                                (the members' states are then undefined) */
 
+/* particle update precision in the 32- and 16-bit storage modes */
+#define PIBM_PARTICLE_FP64 0
+#define PIBM_PARTICLE_FP32 1
+
 /* lattices (value = number of velocities q) */
 #define PIBM_D2Q9 9
 #define PIBM_D3Q15 15
@@ -174,6 +178,14 @@ typedef struct pibm_config {
                           follows both. Every cell's arithmetic is unchanged. Supported
                           with 32- or 64-bit storage and without ordered spreading
                           (deterministic); elsewhere the step runs on one stream. */
+  int particle_update; /* 32- and 16-bit storage: PIBM_PARTICLE_FP64 (0, default) forms
+                          U' - U and the force density g (Eqs. 6, 7, 13) in FP64 from the
+                          FP64 mass, A_p, buoyancy and contact force, with the
+                          interpolated rho_l, j_l widened from FP32; PIBM_PARTICLE_FP32
+                          (1) forms them in FP32 and adds the increment to the FP64 state
+                          (about 6 % faster per step on the 2048^2 workload). Positions
+                          and velocities are FP64 state either way. FP64 storage always
+                          updates in FP64. */
 } pibm_config;
 
 typedef struct pibm_t pibm_t; /* opaque handle owning the device state */

@@ -28,6 +28,7 @@ PIBM_FP64, PIBM_FP32, PIBM_FP16, PIBM_BF16 = 0, 1, 2, 3
 PIBM_INTERP_DELTA, PIBM_INTERP_LAGRANGE4 = 0, 1
 PIBM_DEM_LINEAR, PIBM_DEM_HERTZ = 0, 1
 PIBM_OVERLAP_AUTO, PIBM_OVERLAP_ON, PIBM_OVERLAP_OFF = 0, 1, 2
+PIBM_PARTICLE_FP64, PIBM_PARTICLE_FP32 = 0, 1
 
 FIELD_RHO, FIELD_J, FIELD_POP, FIELD_X, FIELD_U = (1 << k for k in range(5))
 NFIELDS = 5
@@ -73,6 +74,7 @@ class PibmConfig(ctypes.Structure):
         ("dem_substeps", ctypes.c_int),
         ("rebin_every", ctypes.c_int),
         ("overlap", ctypes.c_int),
+        ("particle_update", ctypes.c_int),
     ]
 
 

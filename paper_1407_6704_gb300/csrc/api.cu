@@ -115,6 +115,8 @@ int validate(const pibm_config* c) {
       return PIBM_EINVAL;
   }
   if (c->dem_substeps < 0 || c->dem_substeps > 4096) return PIBM_EINVAL;
+  if (c->particle_update != PIBM_PARTICLE_FP64 && c->particle_update != PIBM_PARTICLE_FP32)
+    return PIBM_EINVAL;
   if (c->rebin_every < 0 || c->rebin_every > 100000) return PIBM_EINVAL;
   if (c->rebin_every > 1 && c->dem_substeps > 1) return PIBM_ENOTSUP;
   if (c->n_particles > 0) {
@@ -467,6 +469,7 @@ int pibm_create(const pibm_config* cfg, void* workspace, size_t workspace_bytes,
     s.phy.hz_damp = 2.0 * sqrt(5.0 / 6.0) * s.phy.beta;
   }
   s.phy.substeps = cfg->dem_substeps > 1 ? cfg->dem_substeps : 1;
+  s.phy.p64 = cfg->precision != PIBM_FP64 && cfg->particle_update == PIBM_PARTICLE_FP64;
   s.phy.rebin = cfg->rebin_every > 1 ? cfg->rebin_every : 1;
   {
     double dmax = 0.0;

@@ -249,6 +249,8 @@ __global__ void __launch_bounds__(ENS_THREADS, EnsShape<Q, St>::MINB) k_ensemble
   using L = Lattice<Q>;
   constexpr int D = L::D;
   constexpr int R0 = W == 2 ? 1 : 2;  // ordered spreading reach (cells)
+  // FP32 members update their particles in FP64 (the default particle_update)
+  constexpr bool P64 = sizeof(R) == 4;
   __shared__ CoupleArgs sA;
   __shared__ EnsExtra sX;
   __shared__ int s_key;
@@ -417,7 +419,7 @@ __global__ void __launch_bounds__(ENS_THREADS, EnsShape<Q, St>::MINB) k_ensemble
       for_tickets(E.bar, __ldg(o + E.nm), [&](long long t) {
         const int pos = item_pos(o, E.nm, t);
         use(__ldg(E.ord + IK_PART * E.nm + pos), k);
-        couple_at<Q, W, St, FT, false, false>(sA, (t - __ldg(o + pos)) * ENS_THREADS + tid);
+        couple_at<Q, W, St, FT, false, false, P64>(sA, (t - __ldg(o + pos)) * ENS_THREADS + tid);
       });
     }
     if (!sync()) return;
@@ -605,6 +607,7 @@ bool ensemble_persistent_supported(const State* const* s, int n) {
     if (a.phy.lagrange || a.phy.hertz || a.phy.substeps > 1) return false;
     if (a.precision != s[0]->precision || a.phy.width != s[0]->phy.width) return false;
     if (a.geo.ncell > INT_MAX || a.p.np > INT_MAX) return false;
+    if (a.precision == PIBM_FP32 && !a.phy.p64) return false;  // built for the FP64 update
   }
   return pick_kernel(s[0]->precision, s[0]->phy.width) != nullptr;
 }

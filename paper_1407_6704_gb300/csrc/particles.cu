@@ -79,15 +79,21 @@ cudaError_t couple_t(const State& s, cudaStream_t st, int* nk, cudaEvent_t befor
       if (!s.phy.lagrange && A.spread) {
         constexpr int TPC = CoupleWindow<D, W>::TPC;
         const long long groups = (P.ntiles + TPC - 1) / TPC;
-        k_couple_tiles<Q, W, St, FT><<<(unsigned)(groups * TILE_CHUNKS), 256, 0, st>>>(A);
+        const unsigned grid = (unsigned)(groups * TILE_CHUNKS);
+        if (s.phy.p64) k_couple_tiles<Q, W, St, FT, true><<<grid, 256, 0, st>>>(A);
+        else k_couple_tiles<Q, W, St, FT, false><<<grid, 256, 0, st>>>(A);
         tiled = true;
       }
     }
+    // 32- and 16-bit storage: the particle update in FP64 (P64) or FP32
+    constexpr bool NARROW = sizeof(R) == 4;
     if (tiled) {
     } else if (s.phy.lagrange) {
-      k_couple<Q, W, St, FT, true><<<pb, 256, 0, st>>>(A);
+      if (NARROW && s.phy.p64) k_couple<Q, W, St, FT, true, NARROW><<<pb, 256, 0, st>>>(A);
+      else k_couple<Q, W, St, FT, true, false><<<pb, 256, 0, st>>>(A);
     } else {
-      k_couple<Q, W, St, FT, false><<<pb, 256, 0, st>>>(A);
+      if (NARROW && s.phy.p64) k_couple<Q, W, St, FT, false, NARROW><<<pb, 256, 0, st>>>(A);
+      else k_couple<Q, W, St, FT, false, false><<<pb, 256, 0, st>>>(A);
     }
     n += 1;
   } else {

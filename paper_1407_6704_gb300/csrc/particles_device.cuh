@@ -10,6 +10,8 @@
 #include <limits.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "pibm_internal.cuh"
 
 namespace pibm {
@@ -1192,18 +1194,20 @@ __device__ __forceinline__ void move_constants(const CoupleArgs& A, unsigned p, 
 // When the next step keeps the cell list, also writes the particle's sorted
 // record for it (same cell, offset of the new position from that cell) and
 // checks that the particle stays within the skin of that cell.
-template <int D, class St, typename FT>
+// P64: 32- and 16-bit storage with the update formed in FP64 (the FP64 branch,
+// with rho_l, j_l widened from FP32 and the FP64 contact force FCT = double).
+template <int D, class St, typename FT, bool P64 = false, typename FCT = typename St::R>
 __device__ __forceinline__ void advance_particle(const CoupleArgs& A, long long sl, unsigned p,
                                                  const int4& mc, const float4& mf,
                                                  const double (&X)[3], const double (&U)[3],
-                                                 const typename St::R (&Fc)[3], typename St::R rs,
+                                                 const FCT (&Fc)[3], typename St::R rs,
                                                  const typename St::R (&js)[3], FT (&amp)[3]) {
   using R = typename St::R;
   const Geometry& g = A.g;
   const long long np = A.np;
   double Un[3];
   bool bad = false, esc = false;
-  if constexpr (sizeof(R) == 8) {
+  if constexpr (sizeof(R) == 8 || P64) {
     const double mi = A.mass[p], Ap = A.Ap[p], bu = A.buoy[p];
     const double rho_l = (double)St::S + rs;
     double Ub[3];
@@ -1305,7 +1309,7 @@ __device__ __forceinline__ void advance_particle(const CoupleArgs& A, long long 
 // written at its slot, which becomes its storage position for the next step.
 // NC: the moment field is read through the read-only path (it was written by an
 // earlier kernel).
-template <int Q, int W, class St, typename FT, bool LAG, bool NC = true>
+template <int Q, int W, class St, typename FT, bool LAG, bool NC = true, bool P64 = false>
 __device__ __forceinline__ void couple_at(const CoupleArgs& A, long long sl) {
   using L = Lattice<Q>;
   using R = typename St::R;
@@ -1334,13 +1338,14 @@ __device__ __forceinline__ void couple_at(const CoupleArgs& A, long long sl) {
     // particle state after the gathers keeps it out of their registers.
     constexpr bool LATE = D == 2 && sizeof(R) == 4;
     double U[3] = {0.0, 0.0, 0.0};
-    R Fc[3] = {R(0), R(0), R(0)};
+    using FCT = typename std::conditional<P64, double, R>::type;
+    FCT Fc[3] = {FCT(0), FCT(0), FCT(0)};
     auto load_state = [&]() {
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         X[k] = A.X[k * np + p];
         U[k] = A.U[k * np + p];
-        if constexpr (sizeof(R) == 8) Fc[k] = A.Fcout[k * np + sl];
+        if constexpr (sizeof(R) == 8 || P64) Fc[k] = A.Fcout[k * np + sl];
         else Fc[k] = A.Fcf[k * np + sl];
       }
     };
@@ -1352,7 +1357,7 @@ __device__ __forceinline__ void couple_at(const CoupleArgs& A, long long sl) {
     if constexpr (LATE) load_state();
 
     // --- particle update (Eq. 13) and force density (Eqs. 6-7) ---
-    advance_particle<D, St, FT>(A, sl, p, mc, mf, X, U, Fc, rs, js, amp);
+    advance_particle<D, St, FT, P64, FCT>(A, sl, p, mc, mf, X, U, Fc, rs, js, amp);
   }
 
   // --- spreading (Eq. 9) with the delta kernel ---
@@ -1378,10 +1383,10 @@ __device__ __forceinline__ void couple_at(const CoupleArgs& A, long long sl) {
   }
 }
 
-template <int Q, int W, class St, typename FT, bool LAG>
+template <int Q, int W, class St, typename FT, bool LAG, bool P64 = false>
 __global__ void __launch_bounds__(256, sizeof(typename St::R) == 4 ? (Lattice<Q>::D == 2 ? 5 : 3) : 2)
     k_couple(CoupleArgs A) {
-  couple_at<Q, W, St, FT, LAG>(A, blockIdx.x * (long long)blockDim.x + threadIdx.x);
+  couple_at<Q, W, St, FT, LAG, true, P64>(A, blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
 
 // Coupling by tiles (32- and 16-bit storage, delta interpolation, atomic
@@ -1428,7 +1433,7 @@ struct CoupleWindow {
                               (D == 3 ? TD::TZ + W + 1 : 1);
 };
 
-template <int Q, int W, class St, typename FT>
+template <int Q, int W, class St, typename FT, bool P64 = false>
 __global__ void __launch_bounds__(256, Lattice<Q>::D == 3 ? 3 : 4) k_couple_tiles(CoupleArgs A) {
   using R = typename St::R;
   constexpr int D = Lattice<Q>::D;
@@ -1504,19 +1509,21 @@ __global__ void __launch_bounds__(256, Lattice<Q>::D == 3 ? 3 : 4) k_couple_tile
         continue;
       }
       double X2[3] = {0.0, 0.0, 0.0}, U2[3] = {0.0, 0.0, 0.0};
-      R Fc2[3] = {R(0), R(0), R(0)};
+      using FCT = typename std::conditional<P64, double, R>::type;
+      FCT Fc2[3] = {FCT(0), FCT(0), FCT(0)};
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         X2[k] = A.X[k * np + p2];
         U2[k] = A.U[k * np + p2];
-        Fc2[k] = A.Fcf[k * np + s2];
+        if constexpr (P64) Fc2[k] = A.Fcout[k * np + s2];
+        else Fc2[k] = A.Fcf[k * np + s2];
       }
       Taps<W, R> ax, ay, az;
       particle_taps<D, W, false, R>(g, c2, f2, X2, ax, ay, az);
       R rs2, js2[3];
       gather_moments<D, W, R>(A, ax, ay, az, rs2, js2);
       FT amp2[3] = {FT(0), FT(0), FT(0)};
-      advance_particle<D, St, FT>(A, s2, p2, c2, f2, X2, U2, Fc2, rs2, js2, amp2);
+      advance_particle<D, St, FT, P64, FCT>(A, s2, p2, c2, f2, X2, U2, Fc2, rs2, js2, amp2);
       spread_amp<D, W, R, FT>(A, ax, ay, az, amp2);
     }
     return;
@@ -1540,12 +1547,14 @@ __global__ void __launch_bounds__(256, Lattice<Q>::D == 3 ? 3 : 4) k_couple_tile
   FT amp[3] = {FT(0), FT(0), FT(0)};
   if (act) {
     double U[3] = {0.0, 0.0, 0.0};
-    R Fc[3] = {R(0), R(0), R(0)};
+    using FCT = typename std::conditional<P64, double, R>::type;
+    FCT Fc[3] = {FCT(0), FCT(0), FCT(0)};
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       X[k] = A.X[k * np + p];
       U[k] = A.U[k * np + p];
-      Fc[k] = A.Fcf[k * np + sl];
+      if constexpr (P64) Fc[k] = A.Fcout[k * np + sl];
+      else Fc[k] = A.Fcf[k * np + sl];
     }
     R rs = R(0), js[3] = {R(0), R(0), R(0)};
 #pragma unroll 1
@@ -1572,7 +1581,7 @@ __global__ void __launch_bounds__(256, Lattice<Q>::D == 3 ? 3 : 4) k_couple_tile
         }
       }
     }
-    advance_particle<D, St, FT>(A, sl, p, mc, mf, X, U, Fc, rs, js, amp);
+    advance_particle<D, St, FT, P64, FCT>(A, sl, p, mc, mf, X, U, Fc, rs, js, amp);
   }
   // the fixed-point scales: per component, a bound on every node's |sum|
   {

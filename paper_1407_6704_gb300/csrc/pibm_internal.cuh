@@ -279,6 +279,7 @@ struct Physics {
   double disp_skin;       // kept cell list: largest displacement per axis from the position at
                           // the rebuild, (1 - d_max) / 4; bounds the recorded candidates
   float skinf, disp_skinf;  // the same two in FP32 (tests on FP32 offsets)
+  int p64;                // 32- and 16-bit storage: particle update in FP64
 };
 
 // Tile of lattice cells handled by one CTA of the particle kernel.

@@ -44,14 +44,17 @@ class Pibm:
                  precision="fp64", deterministic=False, kn=1e-2, restitution=0.9, x0=None,
                  u0=None, diameter=None, density_ratio=None, f0=None, device=None, stream=None,
                  interp="delta", contact="linear", young=1.0, poisson=0.3, wall_young=None,
-                 wall_poisson=None, substeps=1, rebin_every=1, overlap="auto"):
+                 wall_poisson=None, substeps=1, rebin_every=1, overlap="auto",
+                 particle_update="fp64"):
         """interp: "delta" (the spreading kernel) or "lagrange4" (Eq. 5);
         contact: "linear" (kn) or "hertz" (Eq. 15 with young/poisson of the
         particles and of the walls, default the particles'); both use the
         restitution coefficient; substeps: DEM sub-steps per fluid step;
         rebin_every: cell-list rebuild period in steps (skin-checked);
         overlap: "auto", "on" or "off", the collision of the particle-free tiles
-        and the contact search on a second stream (same results)."""
+        and the contact search on a second stream (same results);
+        particle_update: "fp64" (default) or "fp32", the arithmetic of the
+        particle update in the 32- and 16-bit storage modes."""
         import torch
 
         self._torch = torch
@@ -87,6 +90,8 @@ class Pibm:
             int(rebin_every),
             {"auto": _lib.PIBM_OVERLAP_AUTO, "on": _lib.PIBM_OVERLAP_ON,
              "off": _lib.PIBM_OVERLAP_OFF}[overlap])
+        self.cfg.particle_update = {"fp64": _lib.PIBM_PARTICLE_FP64,
+                                    "fp32": _lib.PIBM_PARTICLE_FP32}[particle_update]
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
             else torch.device(device)
         nbytes = ctypes.c_size_t()

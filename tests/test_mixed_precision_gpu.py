@@ -1,5 +1,6 @@
 """Populations stored in FP16 (f - w scaled by 2^12) and BF16 (f - w) with FP32
-collision and force, particles and contacts in FP64, against the FP64 oracle.
+collision and force, particles and contacts in FP64 (the particle update formed in
+FP64 by default, optionally in FP32), against the FP64 oracle.
 
 Bars, stated per field as a relative error against the FP64 oracle:
 - velocity field, relative L2: FP32 <= 1e-5, FP16 <= 1e-3;
@@ -86,21 +87,24 @@ def slice_32():
 SLICE_BARS = {"fp32": 1e-5, "fp16": 1e-3, "bf16": 1e-2}
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
-def test_storage_modes_on_the_32_cubed_slice_against_the_oracle(slice_32, precision):
+@pytest.mark.parametrize("precision,update", [("fp32", "fp64"), ("fp16", "fp64"),
+                                               ("bf16", "fp64"), ("fp32", "fp32"),
+                                               ("fp16", "fp32")])
+def test_storage_modes_on_the_32_cubed_slice_against_the_oracle(slice_32, precision, update):
     """1000 steps of the 3D workload's slice in each storage mode, in the benchmark's
-    launch configuration (cell list kept for 10 steps), against the FP64 oracle."""
+    launch configuration (cell list kept for 10 steps), against the FP64 oracle;
+    the particle update formed in FP64 (the default) or in FP32."""
     from paper_1407_6704_gb300.pibm import Pibm
 
     c = slice_32
     w = c["w"]
     with Pibm("d3q19", c["n"], w.periodic, w.tau, precision=precision, rebin_every=10,
-              **c["kw"]) as sim:
+              particle_update=update, **c["kw"]) as sim:
         sim.step(1000)
         got = sim.read("rho", "j", "x", "u")
         assert sim.status() == 0
     e = _errors(got, c["rho"], c["j"], c["X"], c["U"], c["X0"])
-    print("32^3 slice", precision, e)
+    print("32^3 slice", precision, "update", update, e)
     assert all(v <= SLICE_BARS[precision] for v in e.values()), e
 
 
