@@ -148,11 +148,21 @@ cudaError_t couple_w(const State& s, cudaStream_t st, int* nk, cudaEvent_t ev) {
 }  // namespace
 
 namespace {
-template <int D, bool HZ>
+template <int D, bool HZ, bool HS>
 void contacts_nb(const CoupleArgs& A, unsigned pb, cudaStream_t st) {
-  if (A.nb_mode == 1) k_contacts<D, false, HZ, 1><<<pb, 256, 0, st>>>(A);
-  else if (A.nb_mode == 2) k_contacts<D, false, HZ, 2><<<pb, 256, 0, st>>>(A);
-  else k_contacts<D, false, HZ, 0><<<pb, 256, 0, st>>>(A);
+  if (A.nb_mode == 1) k_contacts<D, false, HZ, 1, HS><<<pb, 256, 0, st>>>(A);
+  else if (A.nb_mode == 2) k_contacts<D, false, HZ, 2, HS><<<pb, 256, 0, st>>>(A);
+  else k_contacts<D, false, HZ, 0, HS><<<pb, 256, 0, st>>>(A);
+}
+template <int D, bool HZ>
+void contacts_hs(const CoupleArgs& A, bool hs, unsigned pb, cudaStream_t st) {
+  if constexpr (D == 3) {
+    if (hs) {
+      contacts_nb<D, HZ, true>(A, pb, st);
+      return;
+    }
+  }
+  contacts_nb<D, HZ, false>(A, pb, st);
 }
 }  // namespace
 
@@ -161,12 +171,18 @@ cudaError_t launch_contacts(const State& s, cudaStream_t st, int* nk) {
   if (s.p.np == 0 || s.phy.substeps > 1) return cudaSuccess;
   CoupleArgs A = couple_args(s);
   const unsigned pb = blocks_for(s.p.np, 256);
+  const bool hs = contacts_half_shell(s);
+  if (hs) {  // partner forces are added into the array: start from zero
+    const cudaError_t e =
+        cudaMemsetAsync(s.p.Fc, 0, sizeof(double) * s.geo.d * s.p.np, st);
+    if (e != cudaSuccess) return e;
+  }
   if (s.geo.d == 2) {
-    if (s.phy.hertz) contacts_nb<2, true>(A, pb, st);
-    else contacts_nb<2, false>(A, pb, st);
+    if (s.phy.hertz) contacts_hs<2, true>(A, hs, pb, st);
+    else contacts_hs<2, false>(A, hs, pb, st);
   } else {
-    if (s.phy.hertz) contacts_nb<3, true>(A, pb, st);
-    else contacts_nb<3, false>(A, pb, st);
+    if (s.phy.hertz) contacts_hs<3, true>(A, hs, pb, st);
+    else contacts_hs<3, false>(A, hs, pb, st);
   }
   if (nk) *nk += 1;
   return cudaGetLastError();
