@@ -173,3 +173,40 @@ def test_noalloc_size_check_cannot_overflow(lib):
                  (19, (4096, 4096, 2**62)), (15, (1, 1, 2**63 - 1))]:
         n3 = (ctypes.c_int64 * 3)(*n)
         assert lib.pibm_fluid_sums_noalloc(dummy, q, n3, dummy, None) == _lib.PIBM_ETOOBIG, n
+
+
+def test_particle_update_modes(lib):
+    """pibm_config.particle_update: PIBM_PARTICLE_FP64 (0) and PIBM_PARTICLE_FP32 (1)
+    are accepted, anything else is PIBM_EINVAL."""
+    for v, want in [(_lib.PIBM_PARTICLE_FP64, _lib.PIBM_OK), (_lib.PIBM_PARTICLE_FP32, _lib.PIBM_OK),
+                    (2, _lib.PIBM_EINVAL), (-1, _lib.PIBM_EINVAL)]:
+        c, keep = _cfg(particle_update=v)
+        assert _ws(lib, c)[0] == want, v
+
+
+def test_ensemble_and_barrier_entry_points_check_arguments(lib):
+    """Every ensemble entry point rejects a NULL ensemble, and the barrier self-test
+    rejects out-of-range arguments, before any CUDA call."""
+    E = _lib.PIBM_EINVAL
+    vp = ctypes.c_void_p
+    out = vp()
+    n = ctypes.c_int64()
+    ints = (ctypes.c_int * 6)()
+    assert lib.pibm_ensemble_create(None, 0, None, ctypes.byref(out)) == E
+    arr = (vp * 1)(None)
+    assert lib.pibm_ensemble_create(arr, 1, None, ctypes.byref(out)) == E  # NULL member
+    assert lib.pibm_ensemble_step(None, 1) == E
+    assert lib.pibm_ensemble_status(None) == E
+    assert lib.pibm_ensemble_configure(None, 0, 0) == E
+    assert lib.pibm_ensemble_autotune(None, 10, ints) == E
+    assert lib.pibm_ensemble_info(None, ints) == E
+    assert lib.pibm_ensemble_launch_count(None, ctypes.byref(n)) == E
+    assert lib.pibm_ensemble_inject_skip(None, 0, 0.1) == E
+    assert lib.pibm_ensemble_set_mode(None, 1) == E
+    lib.pibm_ensemble_destroy(None)  # a no-op
+    passed = ctypes.c_int(-1)
+    for args in [(0, -1, 1, 0.1), (2, 2, 1, 0.1), (1, -1, 0, 0.1), (1, -1, 1, 0.0),
+                 (1, -1, 1, 11.0)]:
+        assert lib.pibm_grid_barrier_test(*args, ctypes.byref(passed)) == E, args
+    assert lib.pibm_grid_barrier_test(1, -1, 1, 0.1, None) == E
+    assert lib.pibm_strerror(_lib.PIBM_ETIMEOUT).decode().startswith("a grid barrier")
