@@ -824,8 +824,10 @@ __device__ __forceinline__ void contacts_at(const CoupleArgs& A, long long sl) {
   }
 }
 
+// 3D half shell: 64 registers (four CTAs per SM) measured 0.192 ms/step of contacts
+// on the 256^3 workload, against 0.233 at 80 and 0.333 at 128.
 template <int D, bool SUB, bool HZ, int NB, bool HS = false>
-__global__ void __launch_bounds__(256, D == 3 ? 3 : 1) k_contacts(CoupleArgs A) {
+__global__ void __launch_bounds__(256, D == 3 ? (HS ? 4 : 3) : 1) k_contacts(CoupleArgs A) {
   contacts_at<D, SUB, HZ, NB, HS>(A, blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
 
