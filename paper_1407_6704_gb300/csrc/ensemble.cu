@@ -8,10 +8,12 @@
 // particles, a chunk of the cell-list scan, a block of tiles, a group of busy
 // tiles for the moment field, or a run of lattice cells. Items are numbered per
 // member from an offset table (one per item kind), so one phase is a single
-// range [0, total) that the CTAs split into contiguous shares; an item runs the
-// same device function as the corresponding single-simulation kernel
-// (particles_device.cuh, lbm_device.cuh), so a member advanced here follows
-// exactly the arithmetic of the same simulation stepped on its own.
+// range [0, total). Phases of even cost split it into contiguous shares per CTA;
+// the contacts, the moment field and the coupling hand items out from a ticket
+// counter. An item runs the same device function as the corresponding
+// single-simulation kernel (particles_device.cuh, lbm_device.cuh), so a member
+// advanced here follows exactly the arithmetic of the same simulation stepped on
+// its own.
 //
 // Grid barriers wait with a limit (%globaltimer, plus a spin-count cap): a CTA
 // that waits longer sets the barrier's abort word and returns, every other CTA
@@ -89,7 +91,7 @@ struct EnsParams {
   int nm;
   int nsteps;
   int cpi;           // cells per collision item
-  int skip_arrive;   // test hook of the barrier self-test (-1: none)
+  int skip_arrive;   // fault injection for tests: this CTA skips the first barrier (-1: none)
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
