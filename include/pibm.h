@@ -318,12 +318,15 @@ void pibm_ensemble_destroy(pibm_ensemble_t* e);
  * multiple of 256; default 1024). Takes effect at the next launch; the graph
  * captured before is kept only when the shape is unchanged. Errors: PIBM_EINVAL. */
 int pibm_ensemble_configure(pibm_ensemble_t* e, int ctas_per_sm, int cells_per_item);
-/* Pick the persistent launch shape by timing: every candidate (CTAs per SM x
- * cells per item) advances the ensemble by steps_per_candidate steps (real
- * steps: the ensemble moves on by candidates x steps_per_candidate steps in
- * all), timed with events on the ensemble's stream; the fastest is kept.
+/* Pick the persistent launch shape by timing: every candidate (CTAs per SM from
+ * 1 to the largest that fits, x cells per item 256, 512, 1024, 2048, 4096)
+ * advances the ensemble by 10 untimed steps (which capture its graph) and then
+ * by steps_per_candidate steps rounded up to a multiple of 10, timed with
+ * events on the ensemble's stream; the fastest is kept. These are real steps:
+ * the ensemble moves on by candidates x (10 + that rounded count) steps.
  * choice (may be NULL) receives {ctas_per_sm, cells_per_item, candidates}.
- * Synchronises the stream. PIBM_ENOTSUP in branch mode. */
+ * Synchronises the stream. PIBM_ENOTSUP when the members do not qualify for
+ * the persistent mode. */
 int pibm_ensemble_autotune(pibm_ensemble_t* e, int steps_per_candidate, int* choice);
 /* info[6]: {1 persistent / 0 branches, CTAs per SM, largest CTAs per SM that fit,
  * cells per collision item, CTAs of the grid, 1 when the launches replay from a
