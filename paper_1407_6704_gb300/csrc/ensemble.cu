@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(ENS_THREADS, EnsShape<Q, St>::MINB) k_ensemble
   const int tid = threadIdx.x;
 
   for (int k = 0; k < E.nsteps; ++k) {
-    int any = 0, det = 0;
+    int any = 0;
     for (int m = tid; m < E.nm; m += ENS_THREADS) any |= s_np[m] && phase_of(m, k) == 0;
     any = __syncthreads_or(any);
     auto rebuilds = [&](int m) { return s_np[m] && phase_of(m, k) == 0; };
